@@ -1,0 +1,444 @@
+#!/usr/bin/env python
+"""Benchmark of the 2D TK-WFP per-step evaluation loop on GB300.
+
+Workload (default): 10^4 coincident sources/targets equispaced on 6 seeded random ellipses
+(semi-axes 2-8 wavelengths) in a 30x30-wavelength box, signals = sums of three
+Gaussian-enveloped sinusoids (carrier 2 pi rad per unit time), dt = 0.1 (~10 steps per
+period), N_t = 2000, tolerance 1e-6, FP64 path.  A "step" is one pass of the whole
+per-step loop (ingest, local part, self term, type-1 NUFFTs of the current and lagged
+levels, mode and far-history updates, type-2 NUFFT).  The timed window starts after
+L + W steps so that the lagged NUFFT and the far history are active.
+
+Metric: target-updates/s = (targets x timed steps) / time.  `value` is device-timed with
+CUDA events on the plan's stream, inputs resident in HBM; `e2e` is measured through the
+C ABI with host buffers (host->device copy of sigma_n and device->host copy of u_n inside
+the timed region).  `--impl reference` times the FP64 CPU oracle (exact retarded field)
+on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "target-updates/s (M_t x N_t per second), FP64 path, rel L2 <= 1e-6 per step"
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 2 FP64 FMA per clock per SM at the maximum SM clock
+FP32_PEAK_TFLOPS = 152 * 2.07e9 * 256 / 1e12  # 128 FP32 FMA per clock per SM
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="cfg2")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variant")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--profile-steps", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+        return dist, int(os.environ["RANK"]), ws
+    return None, 0, 1
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+        "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for k, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(k)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def part_model(info: dict, M: int, Mt: int, fp64: bool) -> dict:
+    """Algorithmic bytes and flops per launch of each part (the minimum the method moves)."""
+    s = 8 if fp64 else 4          # reduced-precision word
+    c = 2 * s                     # reduced-precision complex
+    W = info["W"]
+    NW = 32 if info["nmax"] <= 32 else 64
+    npair, nm, nf_ = info["n_pairs"], info["n_modes"], info["n_far_modes"]
+    nk, nl = info["n_kappa"], info["n_lambda"]
+    nb, nfg, w = info["nb"], info["nf"], info["kernel_width"]
+    nself, nsoe = info["n_self"], info["n_self_soe"]
+    lag = 1  # timed window is in the lagged regime
+    m = {}
+    m["local"] = (npair * (NW * s + 4) + M * NW * s + Mt * (8 + 8), 2 * npair * info["nmax"])
+    m["self"] = (nself * (nsoe * 16 + W * s + 12), nself * nsoe * (2 * W + 4))
+    m["ingest"] = (M * (8 + 4 + 2 * s), 0)
+    m["combine"] = (Mt * (4 + 4 * 8), Mt * 2)
+    m["spread"] = ((1 + lag) * (nb * nb * s + M * (2 * w * s + 4 + s)), (1 + lag) * 2 * M * w * w)
+    m["modes"] = (nm * ((1 + lag) * (W * c + c) + 4 * 16 + 12 + (1 + lag) * c + c) + nk * 4 * W * s,
+                  nm * (8 * W * (1 + lag) + 16))
+    m["far"] = (nf_ * (nl * 32 + W * c + 16) + nl * W * s, nf_ * nl * (4 * W + 8))
+    m["interp"] = (nb * nb * s + Mt * (2 * w * s + 4 + 8), 2 * Mt * w * w)
+    return {k: {"bytes": int(b), "flops": int(f)} for k, (b, f) in m.items()}
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank: int, world: int, dist):
+    import torch
+    from paper_2604_07170_gb300 import inputs, wfp
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    wl = inputs.make(args.config, seed_offset=rank)
+    M = Mt = wl.M
+    res = {}
+
+    def one(precision: str, K: int, Wm: int, timed_e2e: bool, prof_steps: int):
+        stream = torch.cuda.Stream(device=dev)
+        plan0 = wfp.select_params(wl.meta["box"] / 2, wl.dt, wl.n_steps, wl.band_limit, wl.tol,
+                                  precision=0 if precision == "fp64" else 1)
+        pre = plan0["L"] + plan0["W"] + 1          # reach the lagged / far-history regime
+        e2e_steps = args.e2e_steps if timed_e2e else 0
+        Nt = max(wl.n_steps, pre + Wm + K + prof_steps + e2e_steps)
+        t0 = time.perf_counter()
+        plan = wfp.Plan(wl.src_xy, None, wl.dt, Nt, wl.band_limit, wl.tol,
+                        precision=0 if precision == "fp64" else 1, stream=stream.cuda_stream)
+        plan_s = time.perf_counter() - t0
+        info = plan.info()
+        out = torch.empty(Mt, dtype=torch.float64, device=dev)
+        n = 0
+        chunk = 256
+
+        def run_device(nsteps):
+            nonlocal n
+            done = 0
+            while done < nsteps:
+                k = min(chunk, nsteps - done)
+                sig = torch.from_numpy(wl.sigma(n + 1, n + 1 + k)).to(dev)
+                torch.cuda.synchronize(dev)
+                for i in range(k):
+                    plan.step(sig[i], out)
+                n += k
+                done += k
+
+        run_device(pre + Wm)
+        # timed region: inputs already resident in HBM
+        sig = torch.from_numpy(wl.sigma(n + 1, n + 1 + K)).to(dev)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev.index) as clk:
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for i in range(K):
+                plan.step(sig[i], out)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        n += K
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        r = {"ms": ms, "K": K, "info": info, "plan_s": plan_s, "clocks": clk.summary(), "u_last": out.cpu().numpy(),
+             "n_last": n}
+        # per-part timing with CUDA events on the plan's stream
+        if prof_steps > 0:
+            plan.profile(True)
+            run_device(prof_steps)
+            r["parts"] = plan.profile_read()
+            r["prof_steps"] = prof_steps
+            plan.profile(False)
+        # end to end through the C ABI with host buffers
+        if e2e_steps > 0:
+            sig_h = wl.sigma(n + 1, n + 1 + e2e_steps)
+            u_h = np.empty(Mt)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for i in range(e2e_steps):
+                plan.step(sig_h[i], u_h)
+            torch.cuda.synchronize(dev)
+            r["e2e_s"] = time.perf_counter() - t0
+            r["e2e_steps"] = e2e_steps
+            n += e2e_steps
+        plan.close()
+        return r
+
+    prec = args.precision
+    res["main"] = one(prec, args.steps, args.warmup, True, args.profile_steps)
+    if not args.no_mixed and prec == "fp64":
+        res["mixed"] = one("mixed", min(args.steps, 500), args.warmup, False, args.profile_steps)
+    return wl, res
+
+
+def cpu_oracle_rate(wl, n_eval_hint: int, t_budget: float, step: int):
+    """Oracle throughput (target-updates/s) on the host cores, on a bounded sample."""
+    import oracle
+    rng = np.random.default_rng(0)
+    cores = oracle.num_threads()
+    n = max(cores, 8)
+    while True:
+        idx = rng.choice(wl.M, n, replace=False)
+        ev = np.column_stack([wl.src_xy[idx], np.full(n, step * wl.dt)])
+        t0 = time.perf_counter()
+        oracle.field(wl.src_xy, wl.params, ev, r_coinc=1e-12 * wl.meta["box"])
+        dt = time.perf_counter() - t0
+        if dt > 0.25 * t_budget or n >= n_eval_hint:
+            return n / dt, cores, n, dt
+        n = int(min(n_eval_hint, max(2 * n, n * 0.5 * t_budget / max(dt, 1e-3))))
+
+
+def accuracy_sample(wl, u, n_step, k=16):
+    import oracle
+    rng = np.random.default_rng(1)
+    idx = rng.choice(wl.M, k, replace=False)
+    ev = np.column_stack([wl.src_xy[idx], np.full(k, n_step * wl.dt)])
+    ref = oracle.field(wl.src_xy, wl.params, ev, r_coinc=1e-12 * wl.meta["box"])
+    return float(np.linalg.norm(u[idx] - ref) / np.linalg.norm(ref))
+
+
+def roofline(r: dict, M: int, Mt: int, fp64: bool) -> tuple[dict, dict]:
+    peaks = measured_peaks()
+    model = part_model(r["info"], M, Mt, fp64)
+    parts = r.get("parts", {})
+    per = {}
+    for name, (ms, cnt) in parts.items():
+        if cnt == 0:
+            continue
+        e = {"ms_per_launch": ms / cnt, "launches": cnt}
+        if name in model:
+            b, f = model[name]["bytes"], model[name]["flops"]
+            t = ms / cnt * 1e-3
+            e["GB/s"] = b / t / 1e9
+            e["TFLOP/s"] = f / t / 1e12
+            alu_peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+            tb, tf = b / (peaks["hbm_gbs"] * 1e9), f / (alu_peak * 1e12)
+            e["bound"] = "hbm" if tb >= tf else "alu"
+        per[name] = e
+    ours = {k: v for k, v in per.items() if k in model}
+    dom = max(ours, key=lambda k: ours[k]["ms_per_launch"] * ours[k]["launches"]) if ours else None
+    roof = None
+    if dom:
+        e = ours[dom]
+        traffic = None
+        tj = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tj):
+            with open(tj) as f:
+                tr = json.load(f)
+            key = f"{dom}:{'fp64' if fp64 else 'mixed'}"
+            if key in tr and tr[key].get("source_hash") == source_hash():
+                traffic = tr[key]["bytes_per_launch"]
+        if e["bound"] == "hbm":
+            roof = {"kernel": dom, "bound": "hbm", "achieved": round(e["GB/s"], 1), "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": round(e["GB/s"] / peaks["hbm_gbs"], 4), "traffic": traffic,
+                    "peak_source": peaks["source"]}
+        else:
+            pk = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+            roof = {"kernel": dom, "bound": "alu", "achieved": round(e["TFLOP/s"], 4), "peak": round(pk, 3),
+                    "unit": "TFLOP/s", "frac": round(e["TFLOP/s"] / pk, 4), "traffic": traffic,
+                    "peak_source": "derived: 152 SMs x 2070 MHz x " + ("4 FP64" if fp64 else "256 FP32") + " flop/clk"}
+    return roof, per
+
+
+def source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2604_07170_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        if fn.endswith((".cu", ".h", ".cpp")):
+            with open(os.path.join(d, fn), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def launches_per_step(info: dict, n_self: int) -> int:
+    """Kernels of this library per step in the lagged regime (cuFFT's own kernels not counted):
+    ingest, local, [self], combine, spread x2 (current, lagged), modes, [far], interp, tick."""
+    return 1 + 1 + (1 if n_self > 0 else 0) + 1 + 2 + 1 + (1 if info["far_active"] else 0) + 1 + 1
+
+
+def main():
+    args = parse()
+    dist, rank, world = dist_init()
+    if args.impl == "reference":
+        return run_reference(args, rank, world, dist)
+    wl, res = run_ours(args, rank, world, dist)
+    if rank != 0:
+        return
+    r = res["main"]
+    fp64 = args.precision == "fp64"
+    K = r["K"]
+    value = world * wl.M * K / (r["ms"] * 1e-3)
+    roof, parts = roofline(r, wl.M, wl.M, fp64)
+    fft_ms = sum(parts.get(k, {}).get("ms_per_launch", 0) * parts.get(k, {}).get("launches", 0)
+                 for k in ("fft_type1", "fft_type2"))
+    tot_ms = sum(v["ms_per_launch"] * v["launches"] for v in parts.values())
+    info = r["info"]
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "target-updates/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": r["ms"] / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if fp64 else "f64-state/f32",
+        "data": "synthetic (seeded ellipse geometry, Gaussian-sinusoid signals)",
+        "config": {"workload": f"{args.config}: M={wl.M} coincident sources/targets on ellipses in a "
+                               f"{wl.meta['box']:g}x{wl.meta['box']:g}-wavelength box, dt={wl.dt}, N_t={wl.n_steps}, "
+                               f"tol={wl.tol:g}, {args.precision}",
+                   "timed_steps": [r["n_last"] - K + 1, r["n_last"]],
+                   "l2": "inputs larger than L2 (local weights %.2f GB per step)" % (
+                       info["n_pairs"] * 32 * (8 if fp64 else 4) / 1e9),
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "W": info["W"], "p": info["p"], "L": info["L"], "N_modes_half": info["n_modes"],
+                   "nf": info["nf"], "n_pairs": info["n_pairs"], "n_lambda": info["n_lambda"],
+                   "plan_seconds": round(r["plan_s"], 3), "device_bytes": info["device_bytes"]},
+        "clocks": r["clocks"],
+        "gpu_launches": K * launches_per_step(info, info["n_self"]),
+        "roofline": roof,
+        "fft_time_share": round(fft_ms / tot_ms, 4) if tot_ms else None,
+        "parts_ms_per_step": {k: round(v["ms_per_launch"] * v["launches"] / r["prof_steps"], 5)
+                              for k, v in parts.items()},
+    }
+    if "e2e_s" in r:
+        line["e2e"] = {"value": wl.M * r["e2e_steps"] / r["e2e_s"], "unit": "target-updates/s",
+                       "h2d_bytes_per_step": wl.M * 8, "d2h_bytes_per_step": wl.M * 8}
+    if "mixed" in res:
+        m = res["mixed"]
+        roof_m, parts_m = roofline(m, wl.M, wl.M, False)
+        line["mixed"] = {"value": world * wl.M * m["K"] / (m["ms"] * 1e-3), "ms_per_step": m["ms"] / m["K"],
+                         "roofline": roof_m,
+                         "parts_ms_per_step": {k: round(v["ms_per_launch"] * v["launches"] / m["prof_steps"], 5)
+                                               for k, v in parts_m.items()}}
+    if not args.no_cpu:
+        try:
+            rate, cores, n_ev, dt = cpu_oracle_rate(wl, 512, 20.0, r["n_last"])
+            line["cpu_baseline"] = {"value": rate, "unit": "target-updates/s", "cores": cores, "kind": "oracle",
+                                    "sample": f"{n_ev} random targets of {args.config} at one timed step "
+                                              f"(exact retarded field by quadrature), {dt:.1f} s"}
+            line["accuracy"] = {"rel_l2_vs_oracle": accuracy_sample(wl, r["u_last"], r["n_last"]),
+                                "sample": f"16 random targets at step {r['n_last']}"}
+            if "mixed" in res:
+                line["mixed"]["rel_l2_vs_oracle"] = accuracy_sample(wl, res["mixed"]["u_last"],
+                                                                    res["mixed"]["n_last"])
+        except Exception as e:  # pragma: no cover
+            line["cpu_baseline"] = {"error": str(e)}
+    print(json.dumps(line))
+
+
+def run_reference(args, rank, world, dist):
+    """The FP64 CPU oracle as the reference arm, rank 0 only."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2604_07170_gb300 import inputs
+    wl = inputs.make(args.config)
+    cores = oracle.num_threads()
+    # size each step's sample so that warmup + steps stay within ~2 minutes
+    rng = np.random.default_rng(0)
+    probe = max(cores, 8)
+    idx = rng.choice(wl.M, probe, replace=False)
+    ev = np.column_stack([wl.src_xy[idx], np.full(probe, 900 * wl.dt)])
+    t0 = time.perf_counter()
+    oracle.field(wl.src_xy, wl.params, ev, r_coinc=1e-12 * wl.meta["box"])
+    per_eval = (time.perf_counter() - t0) / probe
+    S = int(max(1, min(wl.M, 120.0 / max(1, args.steps + args.warmup) / per_eval)))
+    steps = np.linspace(800, wl.n_steps, args.steps + args.warmup).astype(int)
+    tot_t, tot_n = 0.0, 0
+    for i, n in enumerate(steps):
+        idx = rng.choice(wl.M, S, replace=False)
+        ev = np.column_stack([wl.src_xy[idx], np.full(S, n * wl.dt)])
+        t0 = time.perf_counter()
+        oracle.field(wl.src_xy, wl.params, ev, r_coinc=1e-12 * wl.meta["box"])
+        if i >= args.warmup:
+            tot_t += time.perf_counter() - t0
+            tot_n += S
+    value = tot_n / tot_t
+    sample = f"{S} random targets per step over {args.steps} steps of {args.config}"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "target-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded ellipse geometry, Gaussian-sinusoid signals)",
+            "config": {"workload": f"{args.config}: M={wl.M}, box {wl.meta['box']:g}, dt={wl.dt}, "
+                                   f"N_t={wl.n_steps}, tol={wl.tol:g}, fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": "target-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "target-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

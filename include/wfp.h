@@ -1,0 +1,187 @@
+/*
+ * wfp.h -- C ABI of the GB300 (sm_103a) evaluator of the 2D free-space wave field of M
+ * point sources, by the truncated-kernel windowed Fourier projection (2D TK-WFP) method of
+ * Al Hassanieh, Greengard & Barnett, "A spectral method for the rapid evaluation of
+ * hyperbolic potentials in two dimensions using windowed Fourier projection".
+ *
+ * Problem (Sec. 1, Eqs. wave2d, solnRep, Green, pointSources): with unit wave speed and
+ * zero initial data, the field at target x_i and time t_n = n dt is
+ *
+ *     u(x_i, t_n) = sum_j int_0^{t_n} G(x_i - y_j, t_n - tau) sigma_j(tau) dtau,
+ *     G(x, t)     = H(t - |x|) / (2 pi sqrt(t^2 - |x|^2)),
+ *
+ * where sigma_j(t) = 0 for t <= 0.  Pairs with coincident source and target are excluded
+ * from the sum, as in the paper's reference formula (Sec. 7, Eq. exactSol).
+ *
+ * Each call of wfp_step takes the M samples sigma_j(t_n) of the current step and returns
+ * u(x_i, t_n) at the Mt targets.  Internally the field is split (Sec. 3, Eq. split) into a
+ * local part (direct quadrature, Sec. 6), a near history (Fourier modes advanced by a Duhamel
+ * recurrence and fed by type-1/type-2 NUFFTs, Sec. 4) and a far history (sum-of-exponentials
+ * recurrences, Sec. 5), all evaluated on the GPU.
+ *
+ * Conventions for every entry point:
+ *   - Return codes only: no exceptions cross the ABI, nothing aborts or traps.
+ *   - The caller owns every buffer it passes; the plan owns all memory it allocates.
+ *   - Coordinates and times are in the caller's units; the library normalises them.
+ *   - After WFP_ECUDA a plan is poisoned: every later call except wfp_destroy returns
+ *     WFP_ESTATE.
+ *   - One plan must not be used from two threads at once; distinct plans are independent.
+ *   - wfp_last_error() returns a thread-local message describing the last failure.
+ */
+#ifndef WFP_H
+#define WFP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WFP_OK = 0,
+    WFP_EINVAL = 1,        /* invalid argument (sizes, NaN/Inf coordinates, dt too coarse for the band limit) */
+    WFP_ENOMEM = 2,        /* device or pinned-host allocation failed; nothing is left allocated */
+    WFP_ECUDA = 3,         /* a CUDA or cuFFT call failed; the plan is poisoned */
+    WFP_ESTATE = 4,        /* call not valid in the plan's state (e.g. step beyond Nt, poisoned plan) */
+    WFP_ETIMEOUT = 5,      /* a bounded device-side wait ran out (server) */
+    WFP_EUNSUPPORTED = 6   /* option combination not supported */
+} wfp_status;
+
+enum { WFP_FP64 = 0, WFP_MIXED = 1 };
+
+/*
+ * Options.  wfp_opts_default() fills every field; zero in a numeric field means "derive".
+ *   precision     WFP_FP64: every step in FP64.  WFP_MIXED: spreading, interpolation, FFTs,
+ *                 FIR taps and local weights in FP32; mode state, its per-step rotation, the
+ *                 sum-of-exponentials recurrences and all accumulations across sources in FP64.
+ *   eps           internal tolerance epsilon; 0 => tol/1000.  b = ln(1/eps) (Sec. 2.1).
+ *   W             blending width in steps, delta = W dt (Eq. W); 0 => ceil(2b/(pi - K0 dt)) (Eq. dt).
+ *   p             interpolation order of the local part (Sec. 6); 0 => 20, lowered (even, >= 8) so
+ *                 that nmax = W + 1 + p/2 <= 32.
+ *   Kf            far-history cut-off wavenumber in normalised units (Sec. 5); 0 => derived from eps.
+ *   upsampfac     NUFFT fine-grid upsampling factor; 0 => 2.0.
+ *   kernel_width  NUFFT spreading-kernel width in grid points; 0 => from eps and upsampfac.
+ *   soe_nodes     Gauss-Legendre nodes per dyadic panel of the far sum of exponentials
+ *                 (Sec. 2.3, Eq. LaplaceApprox); 0 => the smallest of 16..32 meeting eps.
+ *   exclude_self  1 (default): for a target coincident with a source (distance <= 1e-12 of the
+ *                 domain size) the self term is excluded, as in Eq. exactSol.
+ *   stream        cudaStream_t to run on, or NULL for a plan-owned stream.
+ *   use_graph     1 (default): the per-step device work is captured once into a CUDA graph.
+ */
+typedef struct {
+    int precision;
+    double eps;
+    int W;
+    int p;
+    double Kf;
+    double upsampfac;
+    int kernel_width;
+    int soe_nodes;
+    int exclude_self;
+    void* stream;
+    int use_graph;
+} wfp_opts;
+
+/*
+ * Derived parameters of a plan (normalised units: the bounding square of all points is
+ * mapped onto B = [-1,1]^2 by x -> (x - c) * scale, t -> t * scale; the field is invariant).
+ */
+typedef struct {
+    double scale, cx, cy;            /* normalisation */
+    double dt, T, K0;                /* normalised step, end time, band limit */
+    double eps, b;                   /* tolerance, KB shape parameter */
+    int W, p, nmax;                  /* blending width (steps), interpolation order, local levels */
+    double delta, K, A, Aplus, dk;   /* Eqs. W, K, A, Ap, dk */
+    int L;                           /* lag in steps: A+ - delta = L dt */
+    double Kf;                       /* far cut-off */
+    int Nh;                          /* modes n in [-Nh, Nh]^2 */
+    int64_t n_modes, n_far_modes;    /* half-plane disk modes (near), (far) */
+    int64_t n_kappa;                 /* distinct |k| among near modes */
+    int n_lambda, soe_panels, soe_nodes;  /* far sum of exponentials */
+    int n_self_soe;                  /* self-term sum of exponentials */
+    int nf, nb, kernel_width;        /* NUFFT fine grid, band, spreading width */
+    double upsampfac;
+    int64_t n_pairs;                 /* local source-target pairs */
+    int64_t n_self;                  /* coincident targets */
+    int lag_active, far_active;
+    int precision;
+    int64_t device_bytes;            /* device memory held by the plan */
+} wfp_info;
+
+typedef struct wfp_plan_s* wfp_plan;
+
+/* Fill *opts with the defaults described above. */
+void wfp_opts_default(wfp_opts* opts);
+
+/*
+ * Create a plan (Sec. 1 problem statement; parameters per Secs. 2-6).
+ *   M, src_xy     number of sources (>= 1) and their coordinates, 2*M doubles interleaved (x, y),
+ *                 host memory, read during the call only.
+ *   Mt, tgt_xy    number of targets (>= 1) and coordinates (host, 2*Mt doubles); may alias src_xy.
+ *   dt, Nt        time step (> 0) and the number of steps the plan will be stepped (>= 1).
+ *   band_limit    K0, the epsilon-bandwidth of the signals in rad per unit time (Thm. 4.1);
+ *                 K0 * dt must be below pi - 2b/W for some W <= 64 (Eq. dt), else WFP_EINVAL.
+ *   tol           target accuracy of the field (e.g. 1e-6); 0 < tol < 1.
+ *   opts          NULL for defaults.
+ *   out           receives the plan handle (NULL on failure).
+ * Errors: WFP_EINVAL (bad sizes / NaN / Inf / dt too coarse), WFP_ENOMEM, WFP_ECUDA.
+ * The call runs the plan-time precomputation (neighbour lists, local weights, FIR taps,
+ * Hankel coefficients, NUFFT set-up) on the current CUDA device and synchronises.
+ */
+wfp_status wfp_plan_create(int64_t M, const double* src_xy, int64_t Mt, const double* tgt_xy, double dt,
+                           int64_t Nt, double band_limit, double tol, const wfp_opts* opts, wfp_plan* out);
+
+/*
+ * Advance one step (Secs. 4.3, 5.1, 6): ingest sigma_j(t_n), n = 1, 2, ..., Nt, and write
+ * u(x_i, t_n).
+ *   sigma_n   M doubles (host or device pointer; detected with cudaPointerGetAttributes).
+ *   u_n       Mt doubles (host or device pointer).
+ * With host pointers the call returns when u_n is written.  With device pointers the work
+ * is ordered on the plan's stream and the call returns after enqueueing it.
+ * Errors: WFP_EINVAL (NULL pointer), WFP_ESTATE (more than Nt steps, poisoned plan), WFP_ECUDA.
+ */
+wfp_status wfp_step(wfp_plan plan, const double* sigma_n, double* u_n);
+
+/* Free everything the plan holds.  NULL is accepted. */
+wfp_status wfp_destroy(wfp_plan plan);
+
+/* Derived parameters and memory footprint of a plan. */
+wfp_status wfp_plan_get_info(wfp_plan plan, wfp_info* info);
+
+/*
+ * Per-part outputs of the last completed step, for diagnostics (host arrays of Mt doubles,
+ * any may be NULL): u_local (Sec. 6, Eq. ul), u_hist (near + far history, Eqs. unh + ufh,
+ * including the self contribution of coincident pairs), u_self (the coincident-pair term
+ * subtracted when exclude_self is set).  u = u_local + u_hist - u_self.
+ */
+wfp_status wfp_step_components(wfp_plan plan, double* u_local, double* u_hist, double* u_self);
+
+/*
+ * Per-part timing with CUDA events recorded on the plan's stream around each part of a step
+ * (ingest, local, self, combine, spread, fft_type1, modes, far, fft_type2, interp, copy).
+ * wfp_profile(plan, 1) resets the totals and starts recording (CUDA graphs are bypassed while
+ * recording); wfp_profile(plan, 0) stops.  wfp_profile_read synchronises the stream and returns,
+ * for up to max_parts parts, the part names (static strings), the total milliseconds and the
+ * number of timed launches; *n_parts receives the number of parts.  Any output array may be NULL.
+ */
+wfp_status wfp_profile(wfp_plan plan, int enable);
+wfp_status wfp_profile_read(wfp_plan plan, int max_parts, const char** names, double* total_ms, int64_t* launches,
+                            int* n_parts);
+
+/*
+ * Derived parameters without creating a plan or touching a GPU (host-only):
+ * same arguments as wfp_plan_create except the coordinates, replaced by the half-side
+ * `halfside` of the bounding square.  Fills the normalisation-independent fields of *info.
+ */
+wfp_status wfp_select_params(double halfside, double dt, int64_t Nt, double band_limit, double tol,
+                             const wfp_opts* opts, wfp_info* info);
+
+/* Human-readable name of a status code, and the thread-local message of the last failure. */
+const char* wfp_status_string(wfp_status s);
+const char* wfp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WFP_H */

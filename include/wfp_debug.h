@@ -1,0 +1,49 @@
+/*
+ * wfp_debug.h -- host-only diagnostics of the 2D TK-WFP evaluator (no GPU needed).
+ *
+ * These expose the plan-time quadrature routines that the CUDA path runs on the device, so
+ * that tests on a machine without a GPU can check them against closed forms and against the
+ * independent CPU oracle.  They allocate only host memory and return WFP_EINVAL on bad
+ * arguments; output arrays are owned by the caller.
+ */
+#ifndef WFP_DEBUG_H
+#define WFP_DEBUG_H
+
+#include "wfp.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * Local-part weights eta_l(r), l = 0..nmax-1 with nmax = W + 1 + p/2 (Sec. 6, Eqs. local2,
+ * sigInterp, ul_GL): u_l(t_n) = sum_l eta_l(r) sigma(t_{n-nmax+1+l}) for one source-target pair
+ * at distance r in (0, W dt), including the factor 1/(2 pi).  eps sets the blending-function
+ * shape b = ln(1/eps); band_limit (rad per unit of dt's time) sets the band of the least-squares
+ * interpolation used on the newest delay intervals (a negative value selects Lagrange interpolation
+ * there too); ng is the number of Gauss-Legendre nodes per panel.  eta: nmax doubles.
+ */
+wfp_status wfp_debug_eta(double r, double dt, int W, int p, double eps, double band_limit, int ng, double* eta);
+
+/*
+ * Near-history FIR taps at wavenumber magnitude kappa (Lemma 4.2, Eq. hggrid), dt folded in:
+ * taps[0..W) = p_m, [W..2W) = q_m, [2W..3W) = pA_m, [3W..4W) = qA_m; lagshift = A+ - delta.
+ * rot = {cos(kappa dt), sin(kappa dt)/kappa, kappa sin(kappa dt)}.  taps: 4W doubles, rot: 3.
+ */
+wfp_status wfp_debug_taps(double kappa, double dt, int W, double eps, double lagshift, double* taps, double* rot);
+
+/* Blending function phi_delta(t) and its first two derivatives (Eq. KBblending), b = ln(1/eps). */
+wfp_status wfp_debug_phi(double t, double delta, double eps, double* phi, double* dphi, double* d2phi);
+
+/*
+ * Nodes and weights of the dyadic-panel sum of exponentials (Sec. 2.3, Eq. LaplaceApprox):
+ * panels [0, lmax/2^(panels-1)], ..., [lmax/2, lmax] with ng Gauss-Legendre nodes each.
+ * lam, q: panels*ng doubles each.
+ */
+wfp_status wfp_debug_soe(double lam_max, int panels, int ng, double* lam, double* q);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WFP_DEBUG_H */

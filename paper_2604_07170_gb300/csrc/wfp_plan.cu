@@ -1,0 +1,671 @@
+// Plan-time precomputation of the 2D TK-WFP evaluator (boundary of the per-step path).
+//
+// Normalises the geometry onto B = [-1,1]^2, finds the local source-target pairs, builds the
+// local quadrature weights (Sec. 6), enumerates the near/far Fourier modes with their FIR taps
+// (Sec. 4.2) and Hankel coefficients (Sec. 5, Eq. H), the sums of exponentials (Sec. 2.3), the
+// NUFFT spreading tables and cuFFT plans, and allocates the device state.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "wfp_plan.h"
+#include "wfp_quad.h"
+
+namespace wfp {
+
+#define CK(x)                                                                      \
+    do {                                                                           \
+        cudaError_t e_ = (x);                                                      \
+        if (e_ != cudaSuccess) {                                                   \
+            err = std::string(#x) + ": " + cudaGetErrorString(e_);                 \
+            return (e_ == cudaErrorMemoryAllocation) ? WFP_ENOMEM : WFP_ECUDA;     \
+        }                                                                          \
+    } while (0)
+#define CKF(x)                                                                     \
+    do {                                                                           \
+        cufftResult r_ = (x);                                                      \
+        if (r_ != CUFFT_SUCCESS) {                                                 \
+            err = std::string(#x) + ": cufft error " + std::to_string((int)r_);    \
+            return (r_ == CUFFT_ALLOC_FAILED) ? WFP_ENOMEM : WFP_ECUDA;            \
+        }                                                                          \
+    } while (0)
+
+static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// scoped temporary device buffer
+template <typename T>
+struct Tmp {
+    T* p = nullptr;
+    cudaError_t alloc(size_t n) { return cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)); }
+    ~Tmp() {
+        if (p) cudaFree(p);
+    }
+};
+
+// ------------------------------------------------------------------- neighbour search
+// pass 0: count pairs with 0 < r < delta and record a coincident source (r <= rc);
+// pass 1: write the pairs (source index and FP64 distance) in cell-scan order.
+__global__ void k_nbr(int pass, int64_t Mt, const double2* __restrict__ tgt, const double2* __restrict__ src,
+                      const int* __restrict__ cell_start, int nc, double cs, double delta, double rc,
+                      int* __restrict__ count, int* __restrict__ selfj, int* __restrict__ nself,
+                      const int64_t* __restrict__ rowptr, int* __restrict__ col, double* __restrict__ rr) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Mt) return;
+    double2 x = tgt[i];
+    int cx = min(nc - 1, max(0, (int)floor((x.x + 1.0) / cs)));
+    int cy = min(nc - 1, max(0, (int)floor((x.y + 1.0) / cs)));
+    int cnt = 0, sj = -1, ns = 0;
+    int64_t o = pass ? rowptr[i] : 0;
+    double d2max = delta * delta, rc2 = rc * rc;
+    for (int gy = max(0, cy - 1); gy <= min(nc - 1, cy + 1); gy++)
+        for (int gx = max(0, cx - 1); gx <= min(nc - 1, cx + 1); gx++) {
+            int c = gy * nc + gx;
+            for (int k = cell_start[c]; k < cell_start[c + 1]; k++) {
+                double dx = x.x - src[k].x, dy = x.y - src[k].y;
+                double d2 = dx * dx + dy * dy;
+                if (d2 <= rc2) {
+                    sj = k;
+                    ns++;
+                    continue;
+                }
+                if (d2 < d2max) {
+                    if (pass) {
+                        col[o + cnt] = k;
+                        rr[o + cnt] = sqrt(d2);
+                    }
+                    cnt++;
+                }
+            }
+        }
+    if (!pass) {
+        count[i] = cnt;
+        selfj[i] = sj;
+        nself[i] = ns;
+    }
+}
+
+// ------------------------------------------------------------------- local weights
+template <typename TW>
+__global__ void __launch_bounds__(128) k_eta(int64_t npairs, const double* __restrict__ rr, double dt, int W, int p,
+                                             int nmax, int NW, const double* __restrict__ phicoef,
+                                             const double* __restrict__ gx, const double* __restrict__ gw, int ng,
+                                             const double* __restrict__ wl, const double* __restrict__ Cls,
+                                             TW* __restrict__ eta) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npairs) return;
+    double e[kMaxLevels];
+    eta_weights(rr[k], dt, W, p, nmax, phicoef, gx, gw, ng, wl, Cls, e);
+    for (int l = 0; l < NW; l++) eta[k * NW + l] = (l < nmax) ? (TW)e[l] : (TW)0;
+}
+
+// ------------------------------------------------------------------- FIR taps
+template <typename TT>
+__global__ void k_taps(int64_t nk, const double* __restrict__ kap, double dt, int W, double lagshift, int ngt,
+                       const double* __restrict__ sq, const double* __restrict__ wq, const double* __restrict__ f1,
+                       const double* __restrict__ f2, TT* __restrict__ taps, double* __restrict__ rot) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nk) return;
+    mode_taps<TT>(kap[i], dt, W, lagshift, ngt, sq, wq, f1, f2, taps + i * 4 * W, rot + 3 * i);
+}
+
+// ------------------------------------------------------------------- Hankel coefficients (Eq. H)
+// Tab[l][i] = q_l exp(-A lam_l) I0(lam_l r_i) phi_Delta(A - r_i) r_i w_i on composite GL nodes r_i in [0, A]
+__global__ void k_hankel_tab(int nlam, int nr, const double* __restrict__ lam, const double* __restrict__ q,
+                             const double* __restrict__ rn, const double* __restrict__ rw,
+                             const double* __restrict__ phicoef, double A, double Delta, double* __restrict__ tab) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nlam * nr) return;
+    int l = (int)(t / nr), i = (int)(t % nr);
+    double r = rn[i];
+    double x = A - r;  // phi_Delta(A - r)
+    double ph = (x <= 0.0) ? 0.0 : (x >= Delta ? 1.0 : cheb_phi(phicoef, 2.0 * x / Delta - 1.0));
+    // I0(lam r) exp(-A lam) = [I0(lam r) e^{-lam r}] e^{-lam (A - r)}
+    double lr = lam[l] * r;
+    tab[t] = q[l] * cyl_bessel_i0(lr) * exp(-lam[l] * A) * ph * r * rw[i];
+}
+
+// H[fk][l] = sum_i J0(kappa_fk r_i) Tab[l][i]
+__global__ void k_hankel(int nfk, int nlam, int nr, const double* __restrict__ kap, const double* __restrict__ rn,
+                         const double* __restrict__ tab, double* __restrict__ H) {
+    extern __shared__ double s_j0[];
+    int fk = blockIdx.x;
+    double kp = kap[fk];
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) s_j0[i] = j0(kp * rn[i]);
+    __syncthreads();
+    for (int l = threadIdx.x; l < nlam; l += blockDim.x) {
+        const double* tl = tab + (int64_t)l * nr;
+        double s = 0.0;
+        for (int i = 0; i < nr; i++) s = fma(s_j0[i], tl[i], s);
+        H[(int64_t)fk * nlam + l] = s;
+    }
+}
+
+// ------------------------------------------------------------------- host helpers
+template <typename T>
+static cudaError_t upload(DevArena& mem, T** d, const std::vector<T>& h) {
+    cudaError_t e = mem.alloc(d, h.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+template <typename T>
+static cudaError_t upload_tmp(Tmp<T>& t, const std::vector<T>& h) {
+    cudaError_t e = t.alloc(h.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(t.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// counting sort of points into nc x nc cells of side cs over [-1,1]^2; returns the order
+static void cell_sort(const std::vector<double>& xy, int nc, double cs, std::vector<int>& order,
+                      std::vector<int>& cell_start) {
+    int64_t n = (int64_t)xy.size() / 2;
+    std::vector<int> cid(n);
+    cell_start.assign((size_t)nc * nc + 1, 0);
+    for (int64_t i = 0; i < n; i++) {
+        int cx = std::min(nc - 1, std::max(0, (int)std::floor((xy[2 * i] + 1.0) / cs)));
+        int cy = std::min(nc - 1, std::max(0, (int)std::floor((xy[2 * i + 1] + 1.0) / cs)));
+        cid[i] = cy * nc + cx;
+        cell_start[cid[i] + 1]++;
+    }
+    for (size_t c = 0; c + 1 < cell_start.size(); c++) cell_start[c + 1] += cell_start[c];
+    std::vector<int> fill(cell_start.begin(), cell_start.end() - 1);
+    order.assign(n, 0);
+    for (int64_t i = 0; i < n; i++) order[fill[cid[i]]++] = (int)i;
+}
+
+// footprint origin (band-relative) and kernel values of a point for the NUFFT
+template <typename T>
+static void point_kernel(const Params& P, double xs, double ys, int& off, T* ker) {
+    double ux = (P.dk * xs + kPi) / P.h, uy = (P.dk * ys + kPi) / P.h;
+    int lx = (int)std::ceil(ux - 0.5 * P.w), ly = (int)std::ceil(uy - 0.5 * P.w);
+    for (int i = 0; i < P.w; i++) {
+        ker[i] = (T)es_kernel((lx + i - ux) / (0.5 * P.w), P.beta);
+        ker[P.w + i] = (T)es_kernel((ly + i - uy) / (0.5 * P.w), P.beta);
+    }
+    int ix0 = lx - P.lb0, iy0 = ly - P.lb0;
+    off = (ix0 & 0xffff) | (iy0 << 16);
+}
+
+// ------------------------------------------------------------------- plan build
+template <typename T>
+static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::vector<double>& txy, std::string& err) {
+    using C = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+    Params& P = pl.P;
+    DevArena& mem = pl.mem;
+    const int64_t M = P.M, Mt = P.Mt;
+    pl.M = M;
+    pl.Mt = Mt;
+    pl.NW = (P.nmax <= 32) ? 32 : 64;
+
+    CK(mem.alloc(&pl.d_step, 1));
+    // ---- phi table
+    std::vector<double> phic;
+    build_phi_table(P.b, phic);
+    CK(upload(mem, &pl.d_phicoef, phic));
+
+    // ---- cell sort of sources and targets (cells of side >= delta)
+    int nc = std::max(1, std::min(4096, (int)std::floor(2.0 / P.delta)));
+    double cs = 2.0 / nc;
+    std::vector<int> sorder, scs, torder, tcs;
+    cell_sort(sxy, nc, cs, sorder, scs);
+    cell_sort(txy, nc, cs, torder, tcs);
+    std::vector<double> ss(2 * M), ts(2 * Mt);
+    for (int64_t k = 0; k < M; k++) {
+        ss[2 * k] = sxy[2 * (int64_t)sorder[k]];
+        ss[2 * k + 1] = sxy[2 * (int64_t)sorder[k] + 1];
+    }
+    for (int64_t k = 0; k < Mt; k++) {
+        ts[2 * k] = txy[2 * (int64_t)torder[k]];
+        ts[2 * k + 1] = txy[2 * (int64_t)torder[k] + 1];
+    }
+    CK(upload(mem, &pl.d_src_perm, sorder));
+    CK(upload(mem, &pl.d_tgt_perm, torder));
+
+    // ---- neighbour search (Sec. 6: N_delta = {j : 0 < r_ij < delta})
+    {
+        Tmp<double> d_s, d_t, d_r;
+        Tmp<int> d_cs, d_cnt, d_self, d_ns;
+        CK(upload_tmp(d_s, ss));
+        CK(upload_tmp(d_t, ts));
+        CK(upload_tmp(d_cs, scs));
+        CK(d_cnt.alloc(Mt));
+        CK(d_self.alloc(Mt));
+        CK(d_ns.alloc(Mt));
+        const double rc = 2e-12;  // coincident: distance <= 1e-12 of the domain side
+        k_nbr<<<nblk(Mt, 128), 128>>>(0, Mt, (const double2*)d_t.p, (const double2*)d_s.p, d_cs.p, nc, cs, P.delta,
+                                      rc, d_cnt.p, d_self.p, d_ns.p, nullptr, nullptr, nullptr);
+        CK(cudaGetLastError());
+        std::vector<int> cnt(Mt), selfj(Mt), ns(Mt);
+        CK(cudaMemcpy(cnt.data(), d_cnt.p, Mt * sizeof(int), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(selfj.data(), d_self.p, Mt * sizeof(int), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(ns.data(), d_ns.p, Mt * sizeof(int), cudaMemcpyDeviceToHost));
+        std::vector<int64_t> rowptr(Mt + 1, 0);
+        for (int64_t i = 0; i < Mt; i++) rowptr[i + 1] = rowptr[i] + cnt[i];
+        pl.n_pairs = rowptr[Mt];
+        std::vector<int> st, ssrc;
+        for (int64_t i = 0; i < Mt; i++) {
+            if (ns[i] > 1) {
+                err = "a target coincides with more than one source";
+                return WFP_EUNSUPPORTED;
+            }
+            if (selfj[i] >= 0) {
+                st.push_back((int)i);
+                ssrc.push_back(selfj[i]);
+            }
+        }
+        pl.n_self = P.exclude_self ? (int64_t)st.size() : 0;
+        if (pl.n_self > 0) {
+            CK(upload(mem, &pl.d_self_tgt, st));
+            CK(upload(mem, &pl.d_self_src, ssrc));
+        }
+        CK(upload(mem, &pl.d_rowptr, rowptr));
+        size_t freeb = 0, totb = 0;
+        CK(cudaMemGetInfo(&freeb, &totb));
+        size_t need = (size_t)pl.n_pairs * (sizeof(int) + sizeof(double) + pl.NW * sizeof(T));
+        if (need + (size_t)(1ull << 30) > freeb) {
+            err = "local weights need " + std::to_string(need >> 20) + " MiB of device memory";
+            return WFP_ENOMEM;
+        }
+        CK(mem.alloc(&pl.d_col, pl.n_pairs));
+        CK(d_r.alloc(pl.n_pairs));
+        k_nbr<<<nblk(Mt, 128), 128>>>(1, Mt, (const double2*)d_t.p, (const double2*)d_s.p, d_cs.p, nc, cs, P.delta,
+                                      rc, nullptr, nullptr, nullptr, pl.d_rowptr, pl.d_col, d_r.p);
+        CK(cudaGetLastError());
+        // ---- local weights (Sec. 6)
+        const int ng = 20;
+        std::vector<double> gx(ng), gw(ng), wl(P.p);
+        gauss_legendre(ng, gx.data(), gw.data());
+        lagrange_ref_weights(P.p, wl.data());
+        std::vector<double> bls;
+        const double Omega = std::max(P.K0, 1e-3 / P.dt);
+        build_ls_cheb(P.nmax, P.dt, Omega, kLsIntervals * P.dt, bls);
+        Tmp<double> d_gx, d_gw, d_wl, d_bls;
+        CK(upload_tmp(d_gx, gx));
+        CK(upload_tmp(d_gw, gw));
+        CK(upload_tmp(d_wl, wl));
+        CK(upload_tmp(d_bls, bls));
+        T* eta = nullptr;
+        CK(mem.alloc(&eta, (size_t)pl.n_pairs * pl.NW));
+        pl.d_eta = eta;
+        if (pl.n_pairs > 0) {
+            k_eta<T><<<nblk(pl.n_pairs, 128), 128>>>(pl.n_pairs, d_r.p, P.dt, P.W, P.p, P.nmax, pl.NW, pl.d_phicoef,
+                                                     d_gx.p, d_gw.p, ng, d_wl.p, d_bls.p, eta);
+            CK(cudaGetLastError());
+        }
+        CK(cudaDeviceSynchronize());
+    }
+
+    // ---- near-history modes: half-plane disk |n| dk <= Km, rows n1 = 0..Nh, -Nh..-1, columns n2 ascending
+    const int Nh = P.Nh;
+    const double R2 = (P.Km / P.dk) * (P.Km / P.dk), Rf2 = (P.Kf / P.dk) * (P.Kf / P.dk);
+    const int64_t maxsq = (int64_t)std::floor(R2) + 1;
+    std::vector<int2> modes;
+    std::vector<int> sqidx(maxsq + 1, -1), fsqidx;
+    modes.reserve((size_t)(1.6 * R2) + 16);
+    for (int pass = 0; pass < 2; pass++) {
+        for (int t = 0; t <= 2 * Nh; t++) {
+            int n1 = (t <= Nh) ? t : t - 2 * Nh - 1;
+            int n2max = (int)std::floor(std::sqrt(std::max(0.0, R2 - (double)n1 * n1)));
+            for (int n2 = (n1 >= 0 ? 0 : 1); n2 <= n2max; n2++) {
+                int64_t sq = (int64_t)n1 * n1 + (int64_t)n2 * n2;
+                if ((double)sq > R2) continue;
+                if (pass == 0)
+                    sqidx[sq] = 1;
+                else
+                    modes.push_back(make_int2(n1, n2));
+            }
+        }
+        if (pass == 0) {
+            int nk = 0;
+            for (auto& v : sqidx)
+                if (v >= 0) v = nk++;
+            pl.n_kappa = nk;
+        }
+    }
+    pl.n_modes = (int64_t)modes.size();
+    std::vector<int> mk(pl.n_modes);
+    std::vector<double> kap(pl.n_kappa);
+    for (int64_t sq = 0; sq <= maxsq; sq++)
+        if (sqidx[sq] >= 0) kap[sqidx[sq]] = P.dk * std::sqrt((double)sq);
+    for (int64_t m = 0; m < pl.n_modes; m++)
+        mk[m] = sqidx[(int64_t)modes[m].x * modes[m].x + (int64_t)modes[m].y * modes[m].y];
+    CK(upload(mem, &pl.d_mode_n, modes));
+    CK(upload(mem, &pl.d_mode_k, mk));
+
+    // ---- FIR taps per distinct |k| (Eq. hggrid)
+    {
+        const int ngt = 24;
+        std::vector<double> gx(ngt), gw(ngt), sq(ngt), wq(ngt), f1((size_t)P.W * ngt), f2((size_t)P.W * ngt);
+        gauss_legendre(ngt, gx.data(), gw.data());
+        for (int q = 0; q < ngt; q++) {
+            sq[q] = 0.5 * P.dt * (gx[q] + 1.0);
+            wq[q] = 0.5 * P.dt * gw[q];
+        }
+        for (int m = 0; m < P.W; m++)
+            for (int q = 0; q < ngt; q++) {
+                double d = sq[q] + m * P.dt;
+                f1[(size_t)m * ngt + q] = dphi_host(d, P.delta, P.b);
+                f2[(size_t)m * ngt + q] = d2phi_host(d, P.delta, P.b);
+            }
+        Tmp<double> d_kap, d_sq, d_wq, d_f1, d_f2;
+        CK(upload_tmp(d_kap, kap));
+        CK(upload_tmp(d_sq, sq));
+        CK(upload_tmp(d_wq, wq));
+        CK(upload_tmp(d_f1, f1));
+        CK(upload_tmp(d_f2, f2));
+        T* taps = nullptr;
+        CK(mem.alloc(&taps, (size_t)pl.n_kappa * 4 * P.W));
+        pl.d_taps = taps;
+        CK(mem.alloc(&pl.d_rot, (size_t)pl.n_kappa * 3));
+        k_taps<T><<<nblk(pl.n_kappa, 128), 128>>>(pl.n_kappa, d_kap.p, P.dt, P.W, P.Aplus - P.delta, ngt, d_sq.p,
+                                                  d_wq.p, d_f1.p, d_f2.p, taps, pl.d_rot);
+        CK(cudaGetLastError());
+        CK(cudaDeviceSynchronize());
+    }
+
+    // ---- far history (Sec. 5): far modes |k| <= Kf, SOE (Sec. 2.3), Hankel coefficients, taps
+    if (P.far_active) {
+        std::vector<int> fm, fk;
+        fsqidx.assign((size_t)std::floor(Rf2) + 2, -1);
+        int nfk = 0;
+        for (int64_t m = 0; m < pl.n_modes; m++) {
+            int64_t s2 = (int64_t)modes[m].x * modes[m].x + (int64_t)modes[m].y * modes[m].y;
+            if ((double)s2 <= Rf2) {
+                if (fsqidx[s2] < 0) fsqidx[s2] = -2;  // mark
+                fm.push_back((int)m);
+            }
+        }
+        std::vector<double> fkap;
+        for (size_t s2 = 0; s2 < fsqidx.size(); s2++)
+            if (fsqidx[s2] == -2) {
+                fsqidx[s2] = nfk++;
+                fkap.push_back(P.dk * std::sqrt((double)s2));
+            }
+        for (int m : fm) fk.push_back(fsqidx[(int64_t)modes[m].x * modes[m].x + (int64_t)modes[m].y * modes[m].y]);
+        pl.n_far = (int64_t)fm.size();
+        pl.n_fkappa = nfk;
+        CK(upload(mem, &pl.d_far_mode, fm));
+        CK(upload(mem, &pl.d_far_k, fk));
+        std::vector<double> lam, q;
+        soe_nodes(P.lam_max, P.soe_panels, P.soe_nodes, lam, q);
+        // composite GL in r on [0, A]: 32 panels x 16 nodes
+        const int npan = 32, ngr = 16, nr = npan * ngr;
+        std::vector<double> gx(ngr), gw(ngr), rn(nr), rw(nr);
+        gauss_legendre(ngr, gx.data(), gw.data());
+        for (int k = 0; k < npan; k++)
+            for (int i = 0; i < ngr; i++) {
+                double a = P.A * k / npan, b = P.A * (k + 1) / npan;
+                rn[k * ngr + i] = 0.5 * (b - a) * gx[i] + 0.5 * (b + a);
+                rw[k * ngr + i] = 0.5 * (b - a) * gw[i];
+            }
+        Tmp<double> d_lam, d_q, d_rn, d_rw, d_tab, d_fkap;
+        CK(upload_tmp(d_lam, lam));
+        CK(upload_tmp(d_q, q));
+        CK(upload_tmp(d_rn, rn));
+        CK(upload_tmp(d_rw, rw));
+        CK(upload_tmp(d_fkap, fkap));
+        CK(d_tab.alloc((size_t)P.n_lambda * nr));
+        k_hankel_tab<<<nblk((int64_t)P.n_lambda * nr, 256), 256>>>(P.n_lambda, nr, d_lam.p, d_q.p, d_rn.p, d_rw.p,
+                                                                   pl.d_phicoef, P.A, P.Delta, d_tab.p);
+        CK(cudaGetLastError());
+        CK(mem.alloc(&pl.d_H, (size_t)nfk * P.n_lambda));
+        k_hankel<<<nfk, 256, nr * sizeof(double)>>>(nfk, P.n_lambda, nr, d_fkap.p, d_rn.p, d_tab.p, pl.d_H);
+        CK(cudaGetLastError());
+        // forcing taps c_{l,m} = dt exp(-lam_l ((L+1+m) dt - A)) [phi((W-m) dt) - phi((W-1-m) dt)]
+        std::vector<T> ftap((size_t)P.n_lambda * P.W);
+        std::vector<double> fdec(P.n_lambda);
+        for (int l = 0; l < P.n_lambda; l++) {
+            fdec[l] = std::exp(-lam[l] * P.dt);
+            for (int m = 0; m < P.W; m++) {
+                double dphi = phi_host(phic.data(), (P.W - m) * P.dt, P.delta) -
+                              phi_host(phic.data(), (P.W - 1 - m) * P.dt, P.delta);
+                ftap[(size_t)l * P.W + m] = (T)(P.dt * std::exp(-lam[l] * ((P.L + 1 + m) * P.dt - P.A)) * dphi);
+            }
+        }
+        T* dft = nullptr;
+        CK(upload(mem, &dft, ftap));
+        pl.d_ftap = dft;
+        CK(upload(mem, &pl.d_fdecay, fdec));
+        CK(mem.alloc(&pl.d_B, (size_t)P.n_lambda * pl.n_far));
+        CK(cudaDeviceSynchronize());
+    }
+
+    // ---- self term of coincident pairs: SOE of 1/d on [d_lo, T] with phi(d_lo) <= eps/100
+    if (pl.n_self > 0) {
+        double lo = 0.0, hi = P.delta;
+        for (int it = 0; it < 200; it++) {
+            double mid = 0.5 * (lo + hi);
+            if (phi_host(phic.data(), mid, P.delta) > 1e-2 * P.eps)
+                hi = mid;
+            else
+                lo = mid;
+        }
+        double dlo = std::max(lo, 1e-6 * P.delta);
+        double Tself = std::max(P.T, 2.0 * P.delta);
+        double lmax = 36.0 / dlo;
+        int panels = std::max(2, (int)std::ceil(std::log2(lmax * Tself)) + 1);
+        std::vector<double> lam, q;
+        int chosen = 0;
+        for (int ng : {8, 10, 12, 14, 16, 20, 24, 32}) {
+            soe_nodes(lmax, panels, ng, lam, q);
+            if (soe_max_rel_error(lam, q, 0.0, dlo, Tself) <= 0.1 * P.eps) {
+                chosen = ng;
+                break;
+            }
+        }
+        if (!chosen) {
+            err = "self-term sum of exponentials did not reach the tolerance";
+            return WFP_EINVAL;
+        }
+        pl.n_soe_self = (int)lam.size();
+        std::vector<T> stap((size_t)pl.n_soe_self * P.W);
+        std::vector<double> sdec(pl.n_soe_self), sw(pl.n_soe_self);
+        for (int l = 0; l < pl.n_soe_self; l++) {
+            sdec[l] = std::exp(-lam[l] * P.dt);
+            sw[l] = q[l] / (2.0 * kPi);
+            for (int m = 0; m < P.W; m++) {
+                double dphi = phi_host(phic.data(), (m + 1) * P.dt, P.delta) - phi_host(phic.data(), m * P.dt, P.delta);
+                stap[(size_t)l * P.W + m] = (T)(P.dt * std::exp(-lam[l] * (m + 1) * P.dt) * dphi);
+            }
+        }
+        T* dst = nullptr;
+        CK(upload(mem, &dst, stap));
+        pl.d_stap = dst;
+        CK(upload(mem, &pl.d_sdecay, sdec));
+        CK(upload(mem, &pl.d_sw, sw));
+        CK(mem.alloc(&pl.d_Y, (size_t)pl.n_soe_self * pl.n_self));
+    }
+
+    // ---- NUFFT tables: footprints, kernel values, deconvolution factors, spreading tiles
+    {
+        if (P.nb >= 32768) {
+            err = "NUFFT band too large for 16-bit footprint offsets";
+            return WFP_EUNSUPPORTED;
+        }
+        std::vector<int> soff(M), toff(Mt);
+        std::vector<T> sker((size_t)M * 2 * P.w), tker((size_t)Mt * 2 * P.w);
+        for (int64_t k = 0; k < M; k++) point_kernel<T>(P, ss[2 * k], ss[2 * k + 1], soff[k], &sker[(size_t)k * 2 * P.w]);
+        for (int64_t k = 0; k < Mt; k++)
+            point_kernel<T>(P, ts[2 * k], ts[2 * k + 1], toff[k], &tker[(size_t)k * 2 * P.w]);
+        CK(upload(mem, &pl.d_src_off, soff));
+        CK(upload(mem, &pl.d_tgt_off, toff));
+        T* dsk = nullptr;
+        T* dtk = nullptr;
+        CK(upload(mem, &dsk, sker));
+        CK(upload(mem, &dtk, tker));
+        pl.d_src_ker = dsk;
+        pl.d_tgt_ker = dtk;
+        std::vector<double> psihat;
+        es_kernel_ft(P.w, P.beta, P.h, P.Nh, psihat);
+        std::vector<double> fac(P.Nh + 1);
+        for (int n = 0; n <= P.Nh; n++) fac[n] = ((n & 1) ? -1.0 : 1.0) * P.h / psihat[n];
+        CK(upload(mem, &pl.d_fac, fac));
+        // tiles of the band touched by each source footprint
+        int ntx = P.nb / kTile;
+        std::vector<std::pair<int, int>> ts_pairs;
+        ts_pairs.reserve((size_t)M * 2);
+        for (int64_t k = 0; k < M; k++) {
+            int ix0 = soff[k] & 0xffff, iy0 = soff[k] >> 16;
+            for (int ty = iy0 / kTile; ty <= (iy0 + P.w - 1) / kTile; ty++)
+                for (int tx = ix0 / kTile; tx <= (ix0 + P.w - 1) / kTile; tx++)
+                    ts_pairs.push_back({ty * ntx + tx, (int)k});
+        }
+        std::sort(ts_pairs.begin(), ts_pairs.end());
+        std::vector<int> txy, tptr, tsrc;
+        for (size_t i = 0; i < ts_pairs.size(); i++) {
+            if (i == 0 || ts_pairs[i].first != ts_pairs[i - 1].first) {
+                int t = ts_pairs[i].first;
+                txy.push_back((t % ntx) | ((t / ntx) << 16));
+                tptr.push_back((int)i);
+            }
+            tsrc.push_back(ts_pairs[i].second);
+        }
+        tptr.push_back((int)ts_pairs.size());
+        pl.n_tiles = (int)txy.size();
+        CK(upload(mem, &pl.d_tile_xy, txy));
+        CK(upload(mem, &pl.d_tile_ptr, tptr));
+        CK(upload(mem, &pl.d_tile_src, tsrc));
+    }
+
+    // ---- grids and cuFFT plans (two-stage pruned transforms)
+    {
+        const int64_t nf = P.nf, nh2 = P.nf / 2 + 1, nc1 = P.Nh + 1;
+        T* sp = nullptr;
+        C *tb = nullptr, *tc = nullptr, *td = nullptr, *te = nullptr;
+        T* tf = nullptr;
+        CK(mem.alloc(&sp, (size_t)P.nb * nf));
+        pl.d_sp_cur = sp;
+        CK(mem.alloc(&tb, (size_t)nf * nh2));
+        pl.d_tb_cur = tb;
+        CK(mem.alloc(&tc, (size_t)nf * nc1));
+        pl.d_tc_cur = tc;
+        if (P.lag_active) {
+            CK(mem.alloc(&sp, (size_t)P.nb * nf));
+            pl.d_sp_lag = sp;
+            CK(mem.alloc(&tb, (size_t)nf * nh2));
+            pl.d_tb_lag = tb;
+            CK(mem.alloc(&tc, (size_t)nf * nc1));
+            pl.d_tc_lag = tc;
+        } else {
+            pl.d_tc_lag = pl.d_tc_cur;  // never read while the lag is inactive
+        }
+        CK(mem.alloc(&td, (size_t)nf * nc1));
+        pl.d_td = td;
+        CK(mem.alloc(&te, (size_t)nf * nh2));
+        pl.d_te = te;
+        CK(mem.alloc(&tf, (size_t)P.nb * nf));
+        pl.d_tf = tf;
+        const bool dbl = sizeof(T) == 8;
+        int n[1] = {(int)nf};
+        int emb_r[1] = {(int)nf}, emb_c[1] = {(int)nh2};
+        CKF(cufftPlanMany(&pl.fftA, 1, n, emb_r, 1, (int)nf, emb_c, 1, (int)nh2, dbl ? CUFFT_D2Z : CUFFT_R2C, P.nb));
+        pl.fft_made[0] = true;
+        CKF(cufftPlanMany(&pl.fftB, 1, n, emb_r, (int)nh2, 1, emb_r, (int)nc1, 1, dbl ? CUFFT_Z2Z : CUFFT_C2C,
+                          (int)nc1));
+        pl.fft_made[1] = true;
+        CKF(cufftPlanMany(&pl.fftBi, 1, n, emb_r, (int)nc1, 1, emb_r, (int)nh2, 1, dbl ? CUFFT_Z2Z : CUFFT_C2C,
+                          (int)nc1));
+        pl.fft_made[2] = true;
+        CKF(cufftPlanMany(&pl.fftAi, 1, n, emb_c, 1, (int)nh2, emb_r, 1, (int)nf, dbl ? CUFFT_Z2D : CUFFT_C2R, P.nb));
+        pl.fft_made[3] = true;
+        for (int i = 0; i < 4; i++) {
+            cufftHandle h = (i == 0) ? pl.fftA : (i == 1) ? pl.fftB : (i == 2) ? pl.fftBi : pl.fftAi;
+            CKF(cufftSetStream(h, pl.stream));
+        }
+    }
+
+    // ---- state
+    {
+        T* w = nullptr;
+        CK(mem.alloc(&w, (size_t)M * pl.NW));
+        pl.d_sigwin = w;
+        pl.n_hist = P.lag_active ? P.L + 1 : 1;
+        CK(mem.alloc(&w, (size_t)pl.n_hist * M));
+        pl.d_sighist = w;
+        CK(mem.alloc(&pl.d_sig_in, M));
+        CK(mem.alloc(&pl.d_alpha, pl.n_modes));
+        CK(mem.alloc(&pl.d_alphad, pl.n_modes));
+        C* r = nullptr;
+        CK(mem.alloc(&r, (size_t)P.W * pl.n_modes));
+        pl.d_ring = r;
+        if (P.lag_active) {
+            CK(mem.alloc(&r, (size_t)P.W * pl.n_modes));
+            pl.d_ring_lag = r;
+        } else {
+            pl.d_ring_lag = pl.d_ring;  // never read while the lag is inactive
+        }
+        CK(mem.alloc(&pl.d_uloc, Mt));
+        CK(mem.alloc(&pl.d_uh, Mt));
+        CK(mem.alloc(&pl.d_uself, Mt));
+        CK(mem.alloc(&pl.d_u_out, Mt));
+    }
+    CK(cudaMallocHost(&pl.h_sig, std::max<int64_t>(M, 1) * sizeof(double)));
+    CK(cudaMallocHost(&pl.h_u, std::max<int64_t>(Mt, 1) * sizeof(double)));
+    CK(cudaEventCreateWithFlags(&pl.ev_out, cudaEventDisableTiming));
+    CK(cudaDeviceSynchronize());
+    return WFP_OK;
+}
+
+wfp_status plan_build(Plan& pl, const double* src_xy, const double* tgt_xy, std::string& err) {
+    Params& P = pl.P;
+    const int64_t M = P.M, Mt = P.Mt;
+    // bounding square of all points
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    auto acc = [&](const double* xy, int64_t n) {
+        for (int64_t i = 0; i < n; i++) {
+            xmin = std::min(xmin, xy[2 * i]);
+            xmax = std::max(xmax, xy[2 * i]);
+            ymin = std::min(ymin, xy[2 * i + 1]);
+            ymax = std::max(ymax, xy[2 * i + 1]);
+        }
+    };
+    acc(src_xy, M);
+    acc(tgt_xy, Mt);
+    P.cx = 0.5 * (xmin + xmax);
+    P.cy = 0.5 * (ymin + ymax);
+    double half = 0.5 * std::max(xmax - xmin, ymax - ymin);
+    double mag = std::max({std::fabs(xmin), std::fabs(xmax), std::fabs(ymin), std::fabs(ymax), 1e-300});
+    half = (half > 1e-12 * mag) ? half * (1.0 + 1e-9) : 1.0;
+    wfp_status st = select_params(half, P.dt_user, P.Nt, P.K0_user, P.tol, pl.opts, P, err);
+    if (st != WFP_OK) return st;
+    P.M = M;
+    P.Mt = Mt;
+    P.cx = 0.5 * (xmin + xmax);
+    P.cy = 0.5 * (ymin + ymax);
+    if (P.W > 32) {
+        err = "W > 32 is not supported";
+        return WFP_EUNSUPPORTED;
+    }
+    std::vector<double> sxy(2 * M), txy(2 * Mt);
+    for (int64_t i = 0; i < M; i++) {
+        sxy[2 * i] = (src_xy[2 * i] - P.cx) * P.scale;
+        sxy[2 * i + 1] = (src_xy[2 * i + 1] - P.cy) * P.scale;
+    }
+    for (int64_t i = 0; i < Mt; i++) {
+        txy[2 * i] = (tgt_xy[2 * i] - P.cx) * P.scale;
+        txy[2 * i + 1] = (tgt_xy[2 * i + 1] - P.cy) * P.scale;
+    }
+    return P.precision == WFP_FP64 ? build_t<double>(pl, sxy, txy, err) : build_t<float>(pl, sxy, txy, err);
+}
+
+void plan_free(Plan& pl) {
+    for (int i = 0; i < 4; i++)
+        if (pl.graph_exec[i]) cudaGraphExecDestroy(pl.graph_exec[i]);
+    prof_collect(pl);
+    if (pl.fft_made[0]) cufftDestroy(pl.fftA);
+    if (pl.fft_made[1]) cufftDestroy(pl.fftB);
+    if (pl.fft_made[2]) cufftDestroy(pl.fftBi);
+    if (pl.fft_made[3]) cufftDestroy(pl.fftAi);
+    pl.mem.release();
+    if (pl.h_sig) cudaFreeHost(pl.h_sig);
+    if (pl.h_u) cudaFreeHost(pl.h_u);
+    if (pl.ev_out) cudaEventDestroy(pl.ev_out);
+    if (pl.own_stream && pl.stream) cudaStreamDestroy(pl.stream);
+}
+
+}  // namespace wfp

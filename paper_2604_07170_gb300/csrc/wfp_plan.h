@@ -1,0 +1,181 @@
+// Device-side plan of the 2D TK-WFP evaluator: buffers, tables and state (CUDA path).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "wfp_internal.h"
+
+namespace wfp {
+
+// Device memory owned by a plan; freed in reverse order of allocation.
+struct DevArena {
+    std::vector<void*> ptrs;
+    int64_t bytes = 0;
+    template <typename T>
+    cudaError_t alloc(T** p, size_t count) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+        if (e != cudaSuccess) return e;
+        ptrs.push_back(q);
+        bytes += (int64_t)(count * sizeof(T));
+        *p = (T*)q;
+        return cudaMemsetAsync(q, 0, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    }
+    void release() {
+        for (auto it = ptrs.rbegin(); it != ptrs.rend(); ++it) cudaFree(*it);
+        ptrs.clear();
+        bytes = 0;
+    }
+};
+
+struct Plan {
+    Params P;
+    wfp_opts opts;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool poisoned = false;
+    int64_t step = 0;  // completed steps
+    int device = 0;
+    DevArena mem;
+
+    // step counter on the device (kernels read it, so the step can be captured in a graph)
+    int64_t* d_step = nullptr;
+
+    // ------------------------------------------------------------ geometry (internal order)
+    int64_t M = 0, Mt = 0;
+    int* d_src_perm = nullptr;   // internal source k -> caller index
+    int* d_tgt_perm = nullptr;   // internal target k -> caller index
+    int NW = 32;                 // sigma window length (power of two >= nmax)
+
+    // local part (Sec. 6): CSR by internal target, weights [pair][NW]
+    int64_t n_pairs = 0;
+    int64_t* d_rowptr = nullptr;
+    int* d_col = nullptr;
+    void* d_eta = nullptr;
+
+    // sigma storage
+    void* d_sigwin = nullptr;    // [M][NW] window of the last NW levels (slot = level & (NW-1)), reduced precision
+    void* d_sighist = nullptr;   // [n_hist][M] in the grid precision (slot = level % n_hist)
+    int n_hist = 1;
+    double* d_sig_in = nullptr;  // caller-order sigma_n staged on the device
+
+    // NUFFT (type-1 and type-2)
+    int* d_src_off = nullptr;    // [M] packed (ix0, iy0) band-relative footprint origin
+    void* d_src_ker = nullptr;   // [M][2w] kernel values (x then y), grid precision
+    int* d_tgt_off = nullptr;    // [Mt]
+    void* d_tgt_ker = nullptr;   // [Mt][2w]
+    int n_tiles = 0;             // non-empty spreading tiles
+    int* d_tile_xy = nullptr;    // [n_tiles] packed (tx, ty)
+    int* d_tile_ptr = nullptr;   // [n_tiles + 1]
+    int* d_tile_src = nullptr;   // sources per tile (internal index), fixed order
+    void* d_sp_cur = nullptr;    // [nb][nf] real spread grid (current)
+    void* d_sp_lag = nullptr;    // [nb][nf] real spread grid (lagged)
+    void* d_tb_cur = nullptr;    // [nf][nf/2+1] complex (rows outside the band stay zero)
+    void* d_tb_lag = nullptr;
+    void* d_tc_cur = nullptr;    // [nf][Nh+1] complex: type-1 result before deconvolution
+    void* d_tc_lag = nullptr;
+    void* d_td = nullptr;        // [nf][Nh+1] complex: type-2 coefficients (conjugated)
+    void* d_te = nullptr;        // [nf][nf/2+1] complex
+    void* d_tf = nullptr;        // [nb][nf] real: type-2 grid in the band
+    double* d_fac = nullptr;     // [Nh+1] (-1)^n h / psihat(n)
+    cufftHandle fftA = 0, fftB = 0, fftBi = 0, fftAi = 0;
+    bool fft_made[4] = {false, false, false, false};
+
+    // near-history modes (Sec. 4): half-plane disk, ordered by (row n1, column n2)
+    int64_t n_modes = 0, n_kappa = 0;
+    int2* d_mode_n = nullptr;    // (n1, n2)
+    int* d_mode_k = nullptr;     // distinct-|k| index
+    void* d_taps = nullptr;      // [n_kappa][4W] p, q, pA, qA (Eq. hggrid), step dt folded in
+    double* d_rot = nullptr;     // [n_kappa][3] cos(k dt), sin(k dt)/k, k sin(k dt)
+    double2* d_alpha = nullptr;  // [n_modes]
+    double2* d_alphad = nullptr; // [n_modes]
+    void* d_ring = nullptr;      // [W][n_modes] S at the last W levels (complex, ring precision)
+    void* d_ring_lag = nullptr;  // [W][n_modes] S at the last W lagged levels
+
+    // far history (Sec. 5)
+    int64_t n_far = 0, n_fkappa = 0;
+    int* d_far_mode = nullptr;   // [n_far] mode index
+    int* d_far_k = nullptr;      // [n_far] far-|k| index
+    double* d_H = nullptr;       // [n_fkappa][n_lambda] Hankel coefficients (Eq. H)
+    void* d_ftap = nullptr;      // [n_lambda][W] forcing taps of the recurrence (reduced precision)
+    double* d_fdecay = nullptr;  // [n_lambda] exp(-lambda dt)
+    double2* d_B = nullptr;      // [n_lambda][n_far] scaled far coefficients (Eq. beta0)
+
+    // self term of coincident pairs
+    int64_t n_self = 0;
+    int n_soe_self = 0;
+    int* d_self_tgt = nullptr;   // internal target
+    int* d_self_src = nullptr;   // internal source
+    void* d_stap = nullptr;      // [n_soe_self][W] (reduced precision)
+    double* d_sdecay = nullptr;  // [n_soe_self]
+    double* d_sw = nullptr;      // [n_soe_self] SOE weights / (2 pi)
+    double* d_Y = nullptr;       // [n_soe_self][n_self]
+
+    // outputs (internal target order)
+    double* d_uloc = nullptr;
+    double* d_uh = nullptr;      // u_h at the current step (computed by the previous advance)
+    double* d_uself = nullptr;
+    double* d_u_out = nullptr;   // caller order
+
+    // host staging
+    double* h_sig = nullptr;     // pinned
+    double* h_u = nullptr;       // pinned
+    cudaEvent_t ev_out = nullptr;
+
+    // graphs: 0 output phase, 1 advance without lag, 2 advance with lag, 3 final tick
+    bool use_graph = true;
+    cudaGraphExec_t graph_exec[4] = {nullptr, nullptr, nullptr, nullptr};
+    int graph_uses[4] = {0, 0, 0, 0};
+
+    // phi table (device)
+    double* d_phicoef = nullptr;
+
+    // per-part timing with CUDA events on the plan's stream (graphs are bypassed while enabled)
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_ev;      // pairs (start, stop)
+    std::vector<int> prof_part;            // part id of each pair
+    double prof_ms[16] = {0};
+    int64_t prof_n[16] = {0};
+};
+
+enum ProfPart {
+    PP_INGEST = 0, PP_LOCAL, PP_SELF, PP_COMBINE, PP_SPREAD, PP_FFT1, PP_MODES, PP_FAR, PP_FFT2, PP_INTERP,
+    PP_COPY, PP_NPARTS
+};
+extern const char* const kPartNames[PP_NPARTS];
+
+// Record an event pair around a part when profiling is on.
+struct ProfScope {
+    Plan& pl;
+    int part;
+    cudaEvent_t e1 = nullptr;
+    ProfScope(Plan& p, int part_) : pl(p), part(part_) {
+        if (!pl.prof) return;
+        cudaEvent_t e0;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, pl.stream);
+        pl.prof_ev.push_back(e0);
+        pl.prof_ev.push_back(e1);
+        pl.prof_part.push_back(part);
+    }
+    void stop() {
+        if (pl.prof && e1) cudaEventRecord(e1, pl.stream);
+        e1 = nullptr;
+    }
+    ~ProfScope() { stop(); }
+};
+void prof_collect(Plan& pl);  // synchronise and fold recorded pairs into prof_ms / prof_n
+
+wfp_status plan_build(Plan& pl, const double* src_xy, const double* tgt_xy, std::string& err);
+void plan_free(Plan& pl);
+wfp_status step_output(Plan& pl, std::string& err);   // ingest, local, self, combine (device)
+wfp_status step_advance_body(Plan& pl, bool lag_now, std::string& err);  // NUFFTs, modes, far, interp
+wfp_status step_tick(Plan& pl, std::string& err);     // advance the device step counter
+
+}  // namespace wfp

@@ -1,0 +1,599 @@
+// Per-step kernels of the 2D TK-WFP evaluator (sm_103a).
+//
+// One call of wfp_step at level n (t_n = n dt) runs two phases on the plan's stream:
+//   output : ingest sigma(t_n); local part u_l(t_n) (Sec. 6); coincident-pair self term;
+//            combine u = u_l + u_h - u_self, with u_h(t_n) left by the previous advance.
+//   advance: type-1 NUFFTs of sigma(t_n) and sigma(t_{n-L}) (Sec. 4.3); Duhamel update of
+//            every near-history mode to t_{n+1} (Lemma 4.2, Eq. hggrid); far-history
+//            recurrences (Sec. 5, Eqs. alphaFApprox, beta0); type-2 NUFFT giving u_h(t_{n+1}).
+// Kernels read the level from a device counter so that both phases can be replayed from
+// CUDA graphs.  T is the reduced precision (double on the FP64 path, float on the mixed path);
+// mode state alpha, its rotation, the recurrences and all sums across sources are FP64.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include "wfp_plan.h"
+
+namespace wfp {
+
+template <typename T>
+struct Cplx;
+template <>
+struct Cplx<double> {
+    using type = double2;
+};
+template <>
+struct Cplx<float> {
+    using type = float2;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------------------------------ ingest
+// sigma(t_n) in caller order -> FP64/FP32 window [M][NW] (slot n & (NW-1)) and the level-major
+// history [n_hist][M] in the grid precision (slot n % n_hist) read by both spreads.
+template <typename T>
+__global__ void k_ingest(const int64_t* __restrict__ d_step, int64_t M, const double* __restrict__ sig_in,
+                         const int* __restrict__ perm, T* __restrict__ sigwin, int NW, T* __restrict__ sighist,
+                         int n_hist) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+    int64_t n = *d_step + 1;
+    double s = sig_in[perm[k]];
+    sigwin[k * NW + (n & (NW - 1))] = (T)s;
+    sighist[(n % n_hist) * M + k] = (T)s;
+}
+
+// ------------------------------------------------------------------------------- local part
+// u_l(x_i, t_n) = sum_{j in N_delta(i)} sum_{l=1}^{nmax} eta_l(r_ij) sigma_j(t_{n-nmax+l})  (Sec. 6)
+// One warp per target row; lane = time level, so each pair's weight row and each source's
+// sigma window are read as contiguous 32-element segments.  eta carries the 1/(2 pi).
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    float y = x - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_local(const int64_t* __restrict__ d_step, int64_t Mt,
+                                               const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                                               const T* __restrict__ eta, const T* __restrict__ sigwin, int NW,
+                                               int nmax, double* __restrict__ uloc) {
+    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (row >= Mt) return;
+    int64_t n = *d_step + 1;
+    int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
+    int s0 = (int)((n - nmax + 1 + lane) & (NW - 1));
+    int s1 = (int)((n - nmax + 1 + lane + 32) & (NW - 1));
+    double tot;
+    if constexpr (sizeof(T) == 8) {
+        double acc = 0.0;
+        int64_t p = p0;
+        for (; p + 1 < p1; p += 2) {
+            int j0 = col[p], j1 = col[p + 1];
+            double e0 = eta[p * NW + lane], e1 = eta[(p + 1) * NW + lane];
+            double x0 = sigwin[(int64_t)j0 * NW + s0], x1 = sigwin[(int64_t)j1 * NW + s0];
+            acc = fma(e0, x0, acc);
+            acc = fma(e1, x1, acc);
+            if (NW == 64) {
+                acc = fma(eta[p * NW + lane + 32], sigwin[(int64_t)j0 * NW + s1], acc);
+                acc = fma(eta[(p + 1) * NW + lane + 32], sigwin[(int64_t)j1 * NW + s1], acc);
+            }
+        }
+        if (p < p1) {
+            int j0 = col[p];
+            acc = fma(eta[p * NW + lane], sigwin[(int64_t)j0 * NW + s0], acc);
+            if (NW == 64) acc = fma(eta[p * NW + lane + 32], sigwin[(int64_t)j0 * NW + s1], acc);
+        }
+        tot = acc;
+    } else {
+        // FP32 products, compensated FP32 accumulation per lane, FP64 across lanes
+        float s = 0.f, c = 0.f;
+        int64_t p = p0;
+        for (; p + 1 < p1; p += 2) {
+            int j0 = col[p], j1 = col[p + 1];
+            float e0 = eta[p * NW + lane], e1 = eta[(p + 1) * NW + lane];
+            float x0 = sigwin[(int64_t)j0 * NW + s0], x1 = sigwin[(int64_t)j1 * NW + s0];
+            kahan_add(s, c, e0 * x0);
+            kahan_add(s, c, e1 * x1);
+            if (NW == 64) {
+                kahan_add(s, c, eta[p * NW + lane + 32] * sigwin[(int64_t)j0 * NW + s1]);
+                kahan_add(s, c, eta[(p + 1) * NW + lane + 32] * sigwin[(int64_t)j1 * NW + s1]);
+            }
+        }
+        if (p < p1) {
+            int j0 = col[p];
+            kahan_add(s, c, eta[p * NW + lane] * sigwin[(int64_t)j0 * NW + s0]);
+            if (NW == 64) kahan_add(s, c, eta[p * NW + lane + 32] * sigwin[(int64_t)j0 * NW + s1]);
+        }
+        tot = (double)s - (double)c;
+    }
+    tot = warp_sum(tot);
+    if (lane == 0) uloc[row] = tot;
+}
+
+// -------------------------------------------------------------------------------- self term
+// u_self,i(t_n) = (1/2pi) int_0^t phi(d) sigma_i(t_n - d)/d dd = sum_l (w_l/2pi) Y_l(t_n), with
+// 1/d ~ sum_l w_l exp(-mu_l d) and Y_l(t) = int exp(-mu_l d) phi(d) sigma(t - d) dd advanced by
+// Y_l(t_{n+1}) = exp(-mu_l dt) Y_l(t_n) + sum_{m<W} e_{l,m} sigma(t_{n-m})  (trapezoid on the grid).
+constexpr int kMaxW = 32;     // W <= 32 (the paper uses 10..30)
+constexpr int kMaxWFar = 32;
+
+template <typename T>
+__global__ void k_self(const int64_t* __restrict__ d_step, int64_t n_self, const int* __restrict__ self_tgt,
+                       const int* __restrict__ self_src, const T* __restrict__ sigwin, int NW, int W, int nsoe,
+                       const T* __restrict__ stap, const double* __restrict__ sdecay,
+                       const double* __restrict__ sw, double* __restrict__ Y, double* __restrict__ uself) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_self) return;
+    int64_t n = *d_step + 1;
+    int src = self_src[s];
+    T sig[kMaxW];
+#pragma unroll
+    for (int m = 0; m < kMaxW; m++) sig[m] = (m < W) ? sigwin[(int64_t)src * NW + ((n - m) & (NW - 1))] : (T)0;
+    double u = 0.0;
+    for (int l = 0; l < nsoe; l++) {
+        double y = Y[(int64_t)l * n_self + s];
+        u = fma(sw[l], y, u);
+        T f = 0;
+        const T* e = stap + (int64_t)l * W;
+#pragma unroll
+        for (int m = 0; m < kMaxW; m++)
+            if (m < W) f += e[m] * sig[m];
+        Y[(int64_t)l * n_self + s] = fma(sdecay[l], y, (double)f);
+    }
+    uself[self_tgt[s]] = u;
+}
+
+__global__ void k_combine(int64_t Mt, const int* __restrict__ tgt_perm, const double* __restrict__ uloc,
+                          const double* __restrict__ uh, const double* __restrict__ uself, double* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Mt) return;
+    out[tgt_perm[i]] = uloc[i] + uh[i] - uself[i];
+}
+
+__global__ void k_tick(int64_t* d_step) { *d_step += 1; }
+
+// ------------------------------------------------------------------------------- spreading
+// Type-1 spreading onto the fine-grid band, one CTA per non-empty 32x32 tile; every grid point
+// sums its sources in the tile's fixed order (no atomics), so the current and the lagged
+// transforms of the same level are bit-identical.  Warp w owns rows w, w+8, w+16, w+24; lane = column.
+constexpr int kSpreadChunk = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread(const int64_t* __restrict__ d_step, int lag, int L, int64_t M,
+                                                const T* __restrict__ sighist, int n_hist,
+                                                const int* __restrict__ tile_xy, const int* __restrict__ tile_ptr,
+                                                const int* __restrict__ tile_src, const int* __restrict__ src_off,
+                                                const T* __restrict__ src_ker, int w, T* __restrict__ sp, int nf,
+                                                int lb0) {
+    int64_t n = *d_step + 1;
+    int64_t lev = lag ? n - L : n;
+    if (lev < 1) return;
+    const T* sig = sighist + (lev % n_hist) * M;
+    __shared__ T s_val[kSpreadChunk];
+    __shared__ int s_off[kSpreadChunk];
+    __shared__ T s_ker[kSpreadChunk * 48];
+    int t = blockIdx.x;
+    int txy = tile_xy[t];
+    int tx = txy & 0xffff, ty = txy >> 16;
+    int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    int colb = tx * kTile + lane;
+    T acc[4] = {0, 0, 0, 0};
+    int a0 = tile_ptr[t], a1 = tile_ptr[t + 1];
+    for (int c0 = a0; c0 < a1; c0 += kSpreadChunk) {
+        int cn = min(kSpreadChunk, a1 - c0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < cn; i += blockDim.x) {
+            int s = tile_src[c0 + i];
+            s_val[i] = sig[s];
+            s_off[i] = src_off[s];
+        }
+        for (int i = threadIdx.x; i < cn * 2 * w; i += blockDim.x) {
+            int si = i / (2 * w), e = i - si * 2 * w;
+            s_ker[si * 48 + e] = src_ker[(int64_t)tile_src[c0 + si] * 2 * w + e];
+        }
+        __syncthreads();
+        for (int i = 0; i < cn; i++) {
+            int off = s_off[i];
+            int dx = colb - (off & 0xffff);
+            if ((unsigned)dx < (unsigned)w) {
+                T wx = s_val[i] * s_ker[i * 48 + dx];
+                int dy0 = ty * kTile + wp - (off >> 16);
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    int dy = dy0 + 8 * r;
+                    if ((unsigned)dy < (unsigned)w) acc[r] += wx * s_ker[i * 48 + w + dy];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        int rowb = ty * kTile + wp + 8 * r;
+        sp[(int64_t)rowb * nf + lb0 + colb] = acc[r];
+    }
+}
+
+// ------------------------------------------------------------------------------ mode update
+// For each half-plane mode k = (n1, n2) dk:
+//   S_n = conj(T1[k]) fac(n1) fac(n2)   (type-1 result, deconvolved, shifted by pi)
+//   h = sum_{m<W} p_m S_{n-m} - pA_m S_{n-m-L},  g likewise with q, qA    (Eq. hggrid)
+//   alpha(t+dt)  =  cos(k dt) alpha + sin(k dt)/k alphadot + h            (Eq. alphakEvolution)
+//   alphad(t+dt) = -k sin(k dt) alpha + cos(k dt) alphadot + g
+// and writes the type-2 coefficient (dk/2pi)^2 alpha fac(n1) fac(n2) (conjugated) for the C2C pass.
+template <typename T>
+__global__ void __launch_bounds__(256) k_modes(
+    const int64_t* __restrict__ d_step, int64_t n_modes, int W, int L, int Nh, int nf, const int2* __restrict__ mode_n,
+    const int* __restrict__ mode_k, const double* __restrict__ fac, double coef2,
+    const typename Cplx<T>::type* __restrict__ tc_cur, const typename Cplx<T>::type* __restrict__ tc_lag,
+    typename Cplx<T>::type* __restrict__ ring, typename Cplx<T>::type* __restrict__ ring_lag,
+    const T* __restrict__ taps, const double* __restrict__ rot, double2* __restrict__ alpha,
+    double2* __restrict__ alphad, typename Cplx<T>::type* __restrict__ td) {
+    using C = typename Cplx<T>::type;
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_modes) return;
+    int64_t n = *d_step + 1;
+    bool lag = (n - L >= 1);
+    int2 nn = mode_n[m];
+    int kid = mode_k[m];
+    int row = nn.x < 0 ? nn.x + nf : nn.x;
+    int64_t gi = (int64_t)row * (Nh + 1) + nn.y;
+    double f = fac[nn.x < 0 ? -nn.x : nn.x] * fac[nn.y];
+    int slot = (int)(n % W);
+    {
+        C t = tc_cur[gi];
+        C s;
+        s.x = (T)((double)t.x * f);
+        s.y = (T)(-(double)t.y * f);
+        ring[(int64_t)slot * n_modes + m] = s;
+    }
+    if (lag) {
+        C t = tc_lag[gi];
+        C s;
+        s.x = (T)((double)t.x * f);
+        s.y = (T)(-(double)t.y * f);
+        ring_lag[(int64_t)slot * n_modes + m] = s;
+    }
+    const T* tp = taps + (int64_t)kid * 4 * W;
+    T hx = 0, hy = 0, gx = 0, gy = 0;
+    int sl = slot;
+    for (int j = 0; j < W; j++) {
+        C a = ring[(int64_t)sl * n_modes + m];
+        T p = tp[j], q = tp[W + j];
+        hx += p * a.x;
+        hy += p * a.y;
+        gx += q * a.x;
+        gy += q * a.y;
+        if (lag) {
+            C b = ring_lag[(int64_t)sl * n_modes + m];
+            T pa = tp[2 * W + j], qa = tp[3 * W + j];
+            hx -= pa * b.x;
+            hy -= pa * b.y;
+            gx -= qa * b.x;
+            gy -= qa * b.y;
+        }
+        sl = (sl == 0) ? W - 1 : sl - 1;
+    }
+    double c = rot[3 * kid], sk = rot[3 * kid + 1], ks = rot[3 * kid + 2];
+    double2 a = alpha[m], ad = alphad[m];
+    double2 an, adn;
+    an.x = fma(c, a.x, fma(sk, ad.x, (double)hx));
+    an.y = fma(c, a.y, fma(sk, ad.y, (double)hy));
+    adn.x = fma(-ks, a.x, fma(c, ad.x, (double)gx));
+    adn.y = fma(-ks, a.y, fma(c, ad.y, (double)gy));
+    alpha[m] = an;
+    alphad[m] = adn;
+    double cf = coef2 * f;
+    C o;
+    o.x = (T)(an.x * cf);
+    o.y = (T)(-an.y * cf);
+    td[gi] = o;
+    if (nn.y == 0 && nn.x > 0) {
+        o.y = (T)(an.y * cf);
+        td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
+    }
+}
+
+// ------------------------------------------------------------------------------ far history
+// For each far mode (|k| <= Kf) and SOE term l (Sec. 5):
+//   B_l(t_{n+1}) = exp(-lam_l dt) B_l(t_n) + sum_{m<W} c_{l,m} S_{n-L-m}
+// (trapezoid rule on the grid applied to the blended far kernel, Eq. beta0 with the exp(A lam)
+// scaling carried in B), then alpha_F = sum_l H_l(|k|) B_l (Eq. alphaFApprox) is added to the
+// type-2 coefficient written by k_modes.  Block (32, 8): 32 far modes x 8 groups of terms.
+template <typename T>
+__global__ void __launch_bounds__(256) k_far(const int64_t* __restrict__ d_step, int64_t n_far, int64_t n_modes, int W,
+                                             int L, int Nh, int nf, int nlam, const int* __restrict__ far_mode,
+                                             const int* __restrict__ far_k, const int2* __restrict__ mode_n,
+                                             const double* __restrict__ fac, double coef2,
+                                             const typename Cplx<T>::type* __restrict__ ring_lag,
+                                             const double* __restrict__ H, const T* __restrict__ ftap,
+                                             const double* __restrict__ fdecay, double2* __restrict__ B,
+                                             typename Cplx<T>::type* __restrict__ td) {
+    using C = typename Cplx<T>::type;
+    int64_t n = *d_step + 1;
+    if (n - L < 1) return;
+    __shared__ double2 s_red[8][32];
+    __shared__ C s_S[kMaxWFar][32];
+    int64_t f = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    int g = threadIdx.y;
+    bool valid = f < n_far;
+    int64_t m = valid ? far_mode[f] : 0;
+    // stage the W lagged levels S_{n-L-j} of this block's 32 modes
+    for (int j = g; j < W; j += 8) {
+        int sl = (int)(((n - j) % W + W) % W);
+        C z;
+        z.x = 0;
+        z.y = 0;
+        s_S[j][threadIdx.x] = valid ? ring_lag[(int64_t)sl * n_modes + m] : z;
+    }
+    __syncthreads();
+    double2 aF = make_double2(0.0, 0.0);
+    if (valid) {
+        int fk = far_k[f];
+        const double* Hr = H + (int64_t)fk * nlam;
+        for (int l = g; l < nlam; l += 8) {
+            const T* cl = ftap + (int64_t)l * W;
+            T fx = 0, fy = 0;
+            for (int j = 0; j < W; j++) {
+                T cj = cl[j];
+                C sj = s_S[j][threadIdx.x];
+                fx += cj * sj.x;
+                fy += cj * sj.y;
+            }
+            double2 b = B[(int64_t)l * n_far + f];
+            double d = fdecay[l];
+            b.x = fma(d, b.x, (double)fx);
+            b.y = fma(d, b.y, (double)fy);
+            B[(int64_t)l * n_far + f] = b;
+            double hl = Hr[l];
+            aF.x = fma(hl, b.x, aF.x);
+            aF.y = fma(hl, b.y, aF.y);
+        }
+    }
+    s_red[g][threadIdx.x] = aF;
+    __syncthreads();
+    if (g == 0 && valid) {
+        for (int k = 1; k < 8; k++) {
+            aF.x += s_red[k][threadIdx.x].x;
+            aF.y += s_red[k][threadIdx.x].y;
+        }
+        int2 nn = mode_n[m];
+        int row = nn.x < 0 ? nn.x + nf : nn.x;
+        int64_t gi = (int64_t)row * (Nh + 1) + nn.y;
+        double cf = coef2 * fac[nn.x < 0 ? -nn.x : nn.x] * fac[nn.y];
+        C o = td[gi];
+        o.x = (T)((double)o.x + aF.x * cf);
+        o.y = (T)((double)o.y - aF.y * cf);
+        td[gi] = o;
+        if (nn.y == 0 && nn.x > 0) {
+            int64_t gp = (int64_t)(nf - nn.x) * (Nh + 1);
+            C q = td[gp];
+            q.x = (T)((double)q.x + aF.x * cf);
+            q.y = (T)((double)q.y + aF.y * cf);
+            td[gp] = q;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------- interpolation
+// Type-2 interpolation: u_h(x_i) = sum over the w x w footprint of grid * psi_x psi_y.
+// One warp per target, lane = column offset.
+template <typename T>
+__global__ void __launch_bounds__(256) k_interp(int64_t Mt, const int* __restrict__ tgt_off,
+                                                const T* __restrict__ tgt_ker, int w, const T* __restrict__ tf,
+                                                int nf, int lb0, double* __restrict__ uh) {
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (i >= Mt) return;
+    int off = tgt_off[i];
+    int ix0 = off & 0xffff, iy0 = off >> 16;
+    const T* ker = tgt_ker + i * 2 * w;
+    T v = 0;
+    if (lane < w) {
+        const T* base = tf + (int64_t)iy0 * nf + lb0 + ix0 + lane;
+        for (int dy = 0; dy < w; dy++) v += base[(int64_t)dy * nf] * ker[w + dy];
+        v *= ker[lane];
+    }
+    double tot = warp_sum((double)v);
+    if (lane == 0) uh[i] = tot;
+}
+
+// ================================================================================ drivers
+static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+#define CK(x)                                                                                   \
+    do {                                                                                        \
+        cudaError_t e_ = (x);                                                                   \
+        if (e_ != cudaSuccess) {                                                                \
+            err = std::string(#x) + ": " + cudaGetErrorString(e_);                              \
+            return WFP_ECUDA;                                                                   \
+        }                                                                                       \
+    } while (0)
+#define CKF(x)                                                                                  \
+    do {                                                                                        \
+        cufftResult r_ = (x);                                                                   \
+        if (r_ != CUFFT_SUCCESS) {                                                              \
+            err = std::string(#x) + ": cufft error " + std::to_string((int)r_);                 \
+            return WFP_ECUDA;                                                                   \
+        }                                                                                       \
+    } while (0)
+
+const char* const kPartNames[PP_NPARTS] = {"ingest", "local", "self", "combine", "spread", "fft_type1",
+                                           "modes",  "far",   "fft_type2", "interp", "copy"};
+
+void prof_collect(Plan& pl) {
+    if (pl.prof_ev.empty()) return;
+    cudaStreamSynchronize(pl.stream);
+    for (size_t i = 0; i < pl.prof_part.size(); i++) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pl.prof_ev[2 * i], pl.prof_ev[2 * i + 1]) == cudaSuccess) {
+            pl.prof_ms[pl.prof_part[i]] += ms;
+            pl.prof_n[pl.prof_part[i]] += 1;
+        }
+        cudaEventDestroy(pl.prof_ev[2 * i]);
+        cudaEventDestroy(pl.prof_ev[2 * i + 1]);
+    }
+    pl.prof_ev.clear();
+    pl.prof_part.clear();
+}
+
+template <typename T>
+static wfp_status output_t(Plan& pl, std::string& err) {
+    const Params& P = pl.P;
+    cudaStream_t st = pl.stream;
+    ProfScope ps0(pl, PP_INGEST);
+    k_ingest<T><<<nblk(pl.M, 256), 256, 0, st>>>(pl.d_step, pl.M, pl.d_sig_in, pl.d_src_perm, (T*)pl.d_sigwin,
+                                                   pl.NW, (T*)pl.d_sighist, pl.n_hist);
+    CK(cudaGetLastError());
+    ps0.stop();
+    if (pl.Mt > 0) {
+        ProfScope ps(pl, PP_LOCAL);
+        k_local<T><<<nblk(pl.Mt * 32, 256), 256, 0, st>>>(pl.d_step, pl.Mt, pl.d_rowptr, pl.d_col, (const T*)pl.d_eta,
+                                                          (const T*)pl.d_sigwin, pl.NW, P.nmax, pl.d_uloc);
+        CK(cudaGetLastError());
+    }
+    if (pl.n_self > 0) {
+        ProfScope ps(pl, PP_SELF);
+        k_self<T><<<nblk(pl.n_self, 128), 128, 0, st>>>(pl.d_step, pl.n_self, pl.d_self_tgt, pl.d_self_src,
+                                                        (const T*)pl.d_sigwin, pl.NW, P.W, pl.n_soe_self,
+                                                        (const T*)pl.d_stap, pl.d_sdecay, pl.d_sw, pl.d_Y, pl.d_uself);
+        CK(cudaGetLastError());
+    }
+    {
+        ProfScope ps(pl, PP_COMBINE);
+        k_combine<<<nblk(pl.Mt, 256), 256, 0, st>>>(pl.Mt, pl.d_tgt_perm, pl.d_uloc, pl.d_uh, pl.d_uself,
+                                                    pl.d_u_out);
+        CK(cudaGetLastError());
+    }
+    return WFP_OK;
+}
+
+template <typename T>
+static wfp_status exec_r2c(cufftHandle h, T* in, typename Cplx<T>::type* out);
+template <>
+wfp_status exec_r2c<double>(cufftHandle h, double* in, double2* out) {
+    return cufftExecD2Z(h, in, (cufftDoubleComplex*)out) == CUFFT_SUCCESS ? WFP_OK : WFP_ECUDA;
+}
+template <>
+wfp_status exec_r2c<float>(cufftHandle h, float* in, float2* out) {
+    return cufftExecR2C(h, in, (cufftComplex*)out) == CUFFT_SUCCESS ? WFP_OK : WFP_ECUDA;
+}
+template <typename T>
+static wfp_status exec_c2c(cufftHandle h, typename Cplx<T>::type* in, typename Cplx<T>::type* out, int dir);
+template <>
+wfp_status exec_c2c<double>(cufftHandle h, double2* in, double2* out, int dir) {
+    return cufftExecZ2Z(h, (cufftDoubleComplex*)in, (cufftDoubleComplex*)out, dir) == CUFFT_SUCCESS ? WFP_OK
+                                                                                                   : WFP_ECUDA;
+}
+template <>
+wfp_status exec_c2c<float>(cufftHandle h, float2* in, float2* out, int dir) {
+    return cufftExecC2C(h, (cufftComplex*)in, (cufftComplex*)out, dir) == CUFFT_SUCCESS ? WFP_OK : WFP_ECUDA;
+}
+template <typename T>
+static wfp_status exec_c2r(cufftHandle h, typename Cplx<T>::type* in, T* out);
+template <>
+wfp_status exec_c2r<double>(cufftHandle h, double2* in, double* out) {
+    return cufftExecZ2D(h, (cufftDoubleComplex*)in, out) == CUFFT_SUCCESS ? WFP_OK : WFP_ECUDA;
+}
+template <>
+wfp_status exec_c2r<float>(cufftHandle h, float2* in, float* out) {
+    return cufftExecC2R(h, (cufftComplex*)in, out) == CUFFT_SUCCESS ? WFP_OK : WFP_ECUDA;
+}
+
+template <typename T>
+static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err) {
+    using C = typename Cplx<T>::type;
+    const Params& P = pl.P;
+    cudaStream_t st = pl.stream;
+    const int nh2 = P.nf / 2 + 1;
+    // type-1 spreading: current level and (when active) the lagged level
+    if (pl.n_tiles > 0) {
+        ProfScope ps(pl, PP_SPREAD);
+        k_spread<T><<<pl.n_tiles, 256, 0, st>>>(pl.d_step, 0, P.L, pl.M, (const T*)pl.d_sighist, pl.n_hist,
+                                                pl.d_tile_xy, pl.d_tile_ptr, pl.d_tile_src, pl.d_src_off,
+                                                (const T*)pl.d_src_ker, P.w, (T*)pl.d_sp_cur, P.nf, P.lb0);
+        CK(cudaGetLastError());
+        if (lag_now) {
+            k_spread<T><<<pl.n_tiles, 256, 0, st>>>(pl.d_step, 1, P.L, pl.M, (const T*)pl.d_sighist, pl.n_hist,
+                                                    pl.d_tile_xy, pl.d_tile_ptr, pl.d_tile_src, pl.d_src_off,
+                                                    (const T*)pl.d_src_ker, P.w, (T*)pl.d_sp_lag, P.nf, P.lb0);
+            CK(cudaGetLastError());
+        }
+    }
+    // two-stage pruned FFT: rows of the band (R2C), then the kept columns (C2C, forward)
+    ProfScope psf(pl, PP_FFT1);
+    if (exec_r2c<T>(pl.fftA, (T*)pl.d_sp_cur, (C*)pl.d_tb_cur + (int64_t)P.lb0 * nh2) != WFP_OK) {
+        err = "cufft type-1 row pass failed";
+        return WFP_ECUDA;
+    }
+    if (exec_c2c<T>(pl.fftB, (C*)pl.d_tb_cur, (C*)pl.d_tc_cur, CUFFT_FORWARD) != WFP_OK) {
+        err = "cufft type-1 column pass failed";
+        return WFP_ECUDA;
+    }
+    if (lag_now) {
+        if (exec_r2c<T>(pl.fftA, (T*)pl.d_sp_lag, (C*)pl.d_tb_lag + (int64_t)P.lb0 * nh2) != WFP_OK ||
+            exec_c2c<T>(pl.fftB, (C*)pl.d_tb_lag, (C*)pl.d_tc_lag, CUFFT_FORWARD) != WFP_OK) {
+            err = "cufft lagged type-1 failed";
+            return WFP_ECUDA;
+        }
+    }
+    psf.stop();
+    double coef2 = (P.dk / (2 * kPi)) * (P.dk / (2 * kPi));
+    ProfScope psm(pl, PP_MODES);
+    k_modes<T><<<nblk(pl.n_modes, 256), 256, 0, st>>>(
+        pl.d_step, pl.n_modes, P.W, P.L, P.Nh, P.nf, pl.d_mode_n, pl.d_mode_k, pl.d_fac, coef2, (const C*)pl.d_tc_cur,
+        (const C*)pl.d_tc_lag, (C*)pl.d_ring, (C*)pl.d_ring_lag, (const T*)pl.d_taps, pl.d_rot, pl.d_alpha,
+        pl.d_alphad, (C*)pl.d_td);
+    CK(cudaGetLastError());
+    psm.stop();
+    if (lag_now && P.far_active && pl.n_far > 0) {
+        ProfScope ps(pl, PP_FAR);
+        dim3 blk(32, 8);
+        k_far<T><<<nblk(pl.n_far, 32), blk, 0, st>>>(pl.d_step, pl.n_far, pl.n_modes, P.W, P.L, P.Nh, P.nf,
+                                                      P.n_lambda, pl.d_far_mode, pl.d_far_k, pl.d_mode_n, pl.d_fac,
+                                                      coef2, (const C*)pl.d_ring_lag, pl.d_H, (const T*)pl.d_ftap, pl.d_fdecay,
+                                                      pl.d_B, (C*)pl.d_td);
+        CK(cudaGetLastError());
+    }
+    // type-2: columns (C2C, inverse) then band rows (C2R); the C2R input beyond column Nh is re-zeroed
+    ProfScope ps2(pl, PP_FFT2);
+    if (exec_c2c<T>(pl.fftBi, (C*)pl.d_td, (C*)pl.d_te, CUFFT_INVERSE) != WFP_OK) {
+        err = "cufft type-2 column pass failed";
+        return WFP_ECUDA;
+    }
+    if (nh2 > P.Nh + 1)
+        CK(cudaMemset2DAsync((C*)pl.d_te + (int64_t)P.lb0 * nh2 + (P.Nh + 1), nh2 * sizeof(C), 0,
+                             (nh2 - P.Nh - 1) * sizeof(C), P.nb, st));
+    if (exec_c2r<T>(pl.fftAi, (C*)pl.d_te + (int64_t)P.lb0 * nh2, (T*)pl.d_tf) != WFP_OK) {
+        err = "cufft type-2 row pass failed";
+        return WFP_ECUDA;
+    }
+    ps2.stop();
+    ProfScope psi(pl, PP_INTERP);
+    k_interp<T><<<nblk(pl.Mt * 32, 256), 256, 0, st>>>(pl.Mt, pl.d_tgt_off, (const T*)pl.d_tgt_ker, P.w,
+                                                       (const T*)pl.d_tf, P.nf, P.lb0, pl.d_uh);
+    CK(cudaGetLastError());
+    return WFP_OK;
+}
+
+wfp_status step_output(Plan& pl, std::string& err) {
+    return pl.P.precision == WFP_FP64 ? output_t<double>(pl, err) : output_t<float>(pl, err);
+}
+
+wfp_status step_advance_body(Plan& pl, bool lag_now, std::string& err) {
+    return pl.P.precision == WFP_FP64 ? advance_t<double>(pl, lag_now, err) : advance_t<float>(pl, lag_now, err);
+}
+
+wfp_status step_tick(Plan& pl, std::string& err) {
+    k_tick<<<1, 1, 0, pl.stream>>>(pl.d_step);
+    CK(cudaGetLastError());
+    return WFP_OK;
+}
+
+}  // namespace wfp

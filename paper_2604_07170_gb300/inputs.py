@@ -148,7 +148,7 @@ def band_limit(params: np.ndarray, family: str, eps: float) -> float:
 # ------------------------------------------------------------- named configs
 def make(name: str, seed_offset: int = 0, tol: float = 1e-6) -> Workload:
     """Named workloads (config units: unit wave speed, carrier 2 pi, dt = 0.1 ~ 10 steps/period)."""
-    eps = tol / 100.0
+    eps = tol / 1000.0
     dt = 0.1
     idx = {"cfg1": 0, "cfg2": 1, "cfg3": 2, "cfg4": 3}.get(name, 9)
     rng = np.random.Generator(np.random.PCG64(SEED0 + idx + 1000 * seed_offset))
@@ -183,5 +183,5 @@ def small(M: int, box: float, n_steps: int, seed: int, curve: bool = False, dt: 
         xy = uniform_square(M, box, rng)
     T = n_steps * dt
     par = gauss3_params(M, T if spread is None else spread, rng, lead=lead)
-    return Workload(f"small{M}", xy, par, "gauss3", dt, n_steps, band_limit(par, "gauss3", tol / 100), tol,
+    return Workload(f"small{M}", xy, par, "gauss3", dt, n_steps, band_limit(par, "gauss3", tol / 1000), tol,
                     {"box": box, "seed": seed})
