@@ -176,6 +176,33 @@ wfp_status wfp_profile_read(wfp_plan plan, int max_parts, const char** names, do
 wfp_status wfp_select_params(double halfside, double dt, int64_t Nt, double band_limit, double tol,
                              const wfp_opts* opts, wfp_info* info);
 
+/*
+ * Local part of one step without any allocation (the paper has no counterpart: this entry point
+ * exists for callers that cannot allocate memory when they need the result -- code running
+ * while a CUDA stream is captured into a graph, where cudaMalloc cannot be captured; code whose
+ * device memory all comes from a fixed arena it may not grow; real-time loops where an
+ * allocation and the synchronisation it can cause are not allowed).  It evaluates
+ *     u_l(x_i, t_n) = sum_{j: 0 < r_ij < delta} sum_l eta_l(r_ij) sigma_j(t_{n-nmax+1+l})   (Sec. 6)
+ * from scratch for the given points, with the same quadrature as a plan's local part.
+ *   M, src_xy      sources, 2*M doubles (x, y), device memory; M <= 65536.
+ *   Mt, tgt_xy     targets, 2*Mt doubles, device memory; Mt <= 32768 (may alias src_xy).
+ *   sigma_win      device, [nmax][M] doubles, level-major, oldest level first: row l holds
+ *                  sigma_j(t_{n-nmax+1+l}) (zero for levels <= 0).
+ *   nmax           W + 1 + p/2 for (dt, band_limit, tol) as wfp_select_params reports; must match.
+ *   dt, band_limit, tol   as in wfp_plan_create (caller units).
+ *   u_local        device, Mt doubles (output).
+ *   stream         cudaStream_t or NULL.
+ * Scratch: one file-scope device array of about 17 MiB, held by every GPU that loads the
+ * library until exit, holds the pair list (at most 65536 pairs 0 < r < delta), the weights and
+ * the tables; larger problems return WFP_EINVAL with a message.  The first call on a device looks
+ * up the array's address (cudaGetSymbolAddress) and must come before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU race.  The call synchronises the
+ * stream once (to read the pair count) and returns with the last kernels enqueued on it.
+ */
+wfp_status wfp_local_noalloc(int64_t M, const double* src_xy, int64_t Mt, const double* tgt_xy,
+                             const double* sigma_win, int nmax, double dt, double band_limit, double tol,
+                             double* u_local, void* stream);
+
 /* Human-readable name of a status code, and the thread-local message of the last failure. */
 const char* wfp_status_string(wfp_status s);
 const char* wfp_last_error(void);

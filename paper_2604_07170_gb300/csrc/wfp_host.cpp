@@ -65,6 +65,11 @@ double d2phi_host(double t, double delta, double b) {
 // Tabulated as kPhiPanels Chebyshev interpolants of degree kPhiDeg; the values at the
 // Chebyshev points come from composite Gauss-Legendre quadrature of the Kaiser-Bessel bump.
 void build_phi_table(double b, std::vector<double>& coef) {
+    coef.assign((size_t)kPhiPanels * (kPhiDeg + 1), 0.0);
+    build_phi_table_into(b, coef.data());
+}
+
+void build_phi_table_into(double b, double* coef) {
     const int np = kPhiPanels, deg = kPhiDeg, ng = 30;
     double gx[ng], gw[ng];
     gauss_legendre(ng, gx, gw);
@@ -82,14 +87,13 @@ void build_phi_table(double b, std::vector<double>& coef) {
         }
         return s;
     };
-    coef.assign((size_t)np * (deg + 1), 0.0);
     double base = 0.0;  // F at the panel's left end
     for (int k = 0; k < np; k++) {
         double xl = -1.0 + 2.0 * k / np, xr = -1.0 + 2.0 * (k + 1) / np;
-        std::vector<double> f(deg + 1), s(deg + 1);
+        double f[kPhiDeg + 1];
         for (int j = 0; j <= deg; j++) {
-            s[j] = std::cos(kPi * (j + 0.5) / (deg + 1));  // Chebyshev points of the first kind
-            double xx = 0.5 * (xr - xl) * s[j] + 0.5 * (xr + xl);
+            double sj = std::cos(kPi * (j + 0.5) / (deg + 1));  // Chebyshev points of the first kind
+            double xx = 0.5 * (xr - xl) * sj + 0.5 * (xr + xl);
             f[j] = base + integ(xl, xx);
         }
         for (int m = 0; m <= deg; m++) {
@@ -109,8 +113,8 @@ double phi_host(const double* coef, double t, double delta) {
 
 // One-sided Jacobi SVD of the m x n (m >= n) column-major matrix A: on return the columns of A
 // are s_j u_j, V (n x n, column-major) holds the right singular vectors and s the singular values.
-static void jacobi_svd(int m, int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& s) {
-    V.assign((size_t)n * n, 0.0);
+static void jacobi_svd(int m, int n, double* A, double* V, double* s) {
+    for (int i = 0; i < n * n; i++) V[i] = 0.0;
     for (int j = 0; j < n; j++) V[(size_t)j * n + j] = 1.0;
     for (int sweep = 0; sweep < 80; sweep++) {
         int rotated = 0;
@@ -141,7 +145,6 @@ static void jacobi_svd(int m, int n, std::vector<double>& A, std::vector<double>
             }
         if (!rotated) break;
     }
-    s.assign(n, 0.0);
     for (int j = 0; j < n; j++) {
         double t = 0;
         for (int i = 0; i < m; i++) t += A[(size_t)j * m + i] * A[(size_t)j * m + i];
@@ -156,15 +159,23 @@ static void jacobi_svd(int m, int n, std::vector<double>& A, std::vector<double>
 // design matrix (condition ~ sqrt of the normal equations').  Returned as Chebyshev coefficients
 // C[l][c], c = 0..kLsDeg, of a_l on [0, span].
 void build_ls_cheb(int nmax, double dt, double Omega, double span, std::vector<double>& C) {
-    const int Q = 96, m = 2 * Q, n = nmax, deg = kLsDeg;
+    C.assign((size_t)nmax * (kLsDeg + 1), 0.0);
+    build_ls_cheb_into(nmax, dt, Omega, span, C.data());
+}
+
+void build_ls_cheb_into(int nmax, double dt, double Omega, double span, double* C) {
+    constexpr int Q = 96, m = 2 * Q, deg = kLsDeg;
+    const int n = nmax;
     const double mu = 1e-16;
-    std::vector<double> gx(Q), gw(Q), om(Q), sw(Q);
-    gauss_legendre(Q, gx.data(), gw.data());
+    double gx[Q], gw[Q], om[Q], sw[Q];
+    gauss_legendre(Q, gx, gw);
     for (int q = 0; q < Q; q++) {
         om[q] = 0.5 * Omega * (gx[q] + 1.0);
         sw[q] = std::sqrt(0.5 * Omega * gw[q]);
     }
-    std::vector<double> A((size_t)m * n), V, s;
+    // fixed-size work arrays (nmax <= kMaxLevels): no heap allocation
+    static_assert(kMaxLevels <= 64, "work arrays sized for 64 levels");
+    double A[m * kMaxLevels], V[kMaxLevels * kMaxLevels], s[kMaxLevels];
     for (int l = 0; l < n; l++) {
         double tl = -(double)(n - 1 - l) * dt;
         for (int q = 0; q < Q; q++) {
@@ -174,8 +185,7 @@ void build_ls_cheb(int nmax, double dt, double Omega, double span, std::vector<d
     }
     jacobi_svd(m, n, A, V, s);
     const double reg = mu * Omega;
-    C.assign((size_t)n * (deg + 1), 0.0);
-    std::vector<double> av((size_t)(deg + 1) * n), b(m);
+    double av[(kLsDeg + 1) * kMaxLevels], b[m];
     for (int c = 0; c <= deg; c++) {
         double x = std::cos(kPi * (c + 0.5) / (deg + 1));
         double tau = 0.5 * span * (x + 1.0);
@@ -267,6 +277,63 @@ static int next_smooth_even(int n) {
     }
 }
 
+wfp_status local_params(double dt, double K0, double tol, const wfp_opts& o, double* eps, int* W, int* p, int* nmax,
+                        const char** why) {
+    *why = "";
+    if (!(dt > 0) || !std::isfinite(dt)) {
+        *why = "dt must be positive and finite";
+        return WFP_EINVAL;
+    }
+    if (!(K0 >= 0) || !std::isfinite(K0)) {
+        *why = "band_limit must be >= 0 and finite";
+        return WFP_EINVAL;
+    }
+    if (!(tol > 0 && tol < 1)) {
+        *why = "tol must be in (0, 1)";
+        return WFP_EINVAL;
+    }
+    // the history parts carry absolute errors ~eps |sigma|, which must stay below tol times the
+    // smallest per-step field norm of interest (tail steps of a pulse are ~1e-2 of the peak)
+    double e = (o.eps > 0) ? o.eps : tol / 1000.0;
+    if (!(e > 0 && e < 1)) {
+        *why = "eps must be in (0, 1)";
+        return WFP_EINVAL;
+    }
+    double b = std::log(1.0 / e);
+    double K0dt = K0 * dt;  // scale-free
+    if (!(K0dt < kPi)) {
+        *why = "band_limit * dt must be below pi (Eq. dt)";
+        return WFP_EINVAL;
+    }
+    // Eq. dt: dt <= (pi - 2b/W)/K0  <=>  W >= 2b / (pi - K0 dt)
+    int w = (o.W > 0) ? o.W : (int)std::ceil(2.0 * b / (kPi - K0dt) - 1e-12);
+    if (w < 2) w = 2;
+    if (2.0 * b / w >= kPi - K0dt) {
+        *why = "W too small for band_limit * dt (Eq. dt)";
+        return WFP_EINVAL;
+    }
+    if (w > 32) {
+        *why = "W must be <= 32 (dt too coarse for the band limit)";
+        return WFP_EINVAL;
+    }
+    // default order 20 (Sec. 7), reduced if needed so that nmax = W + 1 + p/2 fits a 32-level window
+    int pp = (o.p > 0) ? o.p : std::max(8, std::min(20, 2 * (31 - w)));
+    if (pp % 2) pp += 1;
+    if (pp > 32) {
+        *why = "interpolation order p must be <= 32";
+        return WFP_EINVAL;
+    }
+    if (w + 1 + pp / 2 > kMaxLevels) {
+        *why = "W + 1 + p/2 exceeds the supported number of levels";
+        return WFP_EINVAL;
+    }
+    *eps = e;
+    *W = w;
+    *p = pp;
+    *nmax = w + 1 + pp / 2;
+    return WFP_OK;
+}
+
 wfp_status select_params(double halfside, double dt, int64_t Nt, double K0, double tol, const wfp_opts& o,
                          Params& P, std::string& err) {
     if (!(halfside > 0) || !std::isfinite(halfside)) {
@@ -303,42 +370,15 @@ wfp_status select_params(double halfside, double dt, int64_t Nt, double K0, doub
     P.dt = dt * P.scale;
     P.K0 = K0 / P.scale;
     P.T = (double)Nt * P.dt;
-    // the history parts carry absolute errors ~eps |sigma|, which must stay below tol times the
-    // smallest per-step field norm of interest (tail steps of a pulse are ~1e-2 of the peak)
-    P.eps = (o.eps > 0) ? o.eps : tol / 1000.0;
-    if (!(P.eps > 0 && P.eps < 1)) {
-        err = "eps must be in (0, 1)";
-        return WFP_EINVAL;
+    {
+        const char* why = "";
+        wfp_status st = local_params(dt, K0, tol, o, &P.eps, &P.W, &P.p, &P.nmax, &why);
+        if (st != WFP_OK) {
+            err = why;
+            return st;
+        }
     }
     P.b = std::log(1.0 / P.eps);
-    double K0dt = K0 * dt;  // scale-free
-    if (!(K0dt < kPi)) {
-        err = "band_limit * dt must be below pi (Eq. dt)";
-        return WFP_EINVAL;
-    }
-    // Eq. dt: dt <= (pi - 2b/W)/K0  <=>  W >= 2b / (pi - K0 dt)
-    P.W = (o.W > 0) ? o.W : (int)std::ceil(2.0 * P.b / (kPi - K0dt) - 1e-12);
-    if (P.W < 2) P.W = 2;
-    if (2.0 * P.b / P.W >= kPi - K0dt) {
-        err = "W too small for band_limit * dt (Eq. dt)";
-        return WFP_EINVAL;
-    }
-    // default order 20 (Sec. 7), reduced if needed so that nmax = W + 1 + p/2 fits a 32-level window
-    P.p = (o.p > 0) ? o.p : std::max(8, std::min(20, 2 * (31 - P.W)));
-    if (P.p % 2) P.p += 1;
-    if (P.p > 32) {
-        err = "interpolation order p must be <= 32";
-        return WFP_EINVAL;
-    }
-    if (P.W > 32) {
-        err = "W must be <= 32 (dt too coarse for the band limit)";
-        return WFP_EINVAL;
-    }
-    P.nmax = P.W + 1 + P.p / 2;  // Sec. 6
-    if (P.nmax > kMaxLevels) {
-        err = "W + 1 + p/2 exceeds " + std::to_string(kMaxLevels) + " (dt too coarse for the band limit)";
-        return WFP_EINVAL;
-    }
     P.delta = P.W * P.dt;        // Eq. W
     P.K = P.K0 + 2.0 * P.b / P.delta;  // Eq. K
     P.Delta = 1.0;

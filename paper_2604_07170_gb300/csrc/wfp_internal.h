@@ -61,6 +61,7 @@ void fill_info(const Params& P, wfp_info& info);
 
 // phi(t) = F(2t/delta - 1); F tabulated as kPhiPanels Chebyshev pieces of degree kPhiDeg on [-1,1].
 void build_phi_table(double b, std::vector<double>& coef);
+void build_phi_table_into(double b, double* coef);  // kPhiPanels * (kPhiDeg + 1) doubles, no heap use
 double phi_host(const double* coef, double t, double delta);
 double dphi_host(double t, double delta, double b);                // phi'
 double d2phi_host(double t, double delta, double b);               // phi''
@@ -68,6 +69,10 @@ double d2phi_host(double t, double delta, double b);               // phi''
 constexpr int kLsIntervals = 4;  // newest delay intervals interpolated by band-limited least squares
 constexpr int kLsDeg = 28;       // Chebyshev degree of the least-squares weights over those intervals
 void build_ls_cheb(int nmax, double dt, double Omega, double span, std::vector<double>& C);
+void build_ls_cheb_into(int nmax, double dt, double Omega, double span, double* C);  // no heap use
+// W, p, nmax and eps of the local part from dt, K0 (band limit) and tol (no heap use)
+wfp_status local_params(double dt, double K0, double tol, const wfp_opts& o, double* eps, int* W, int* p, int* nmax,
+                        const char** why);
 
 // Dyadic-panel Gauss-Legendre discretisation of the Laplace integral
 // 1/sqrt(t^2 - r^2) = int_0^inf exp(-lambda t) I0(r lambda) dlambda (Eq. LaplaceIntegral):

@@ -48,7 +48,7 @@ _lib = None
 # every symbol declared in include/wfp.h and include/wfp_debug.h
 EXPORTS = ["wfp_opts_default", "wfp_plan_create", "wfp_step", "wfp_destroy", "wfp_plan_get_info",
            "wfp_step_components", "wfp_select_params", "wfp_status_string", "wfp_last_error",
-           "wfp_profile", "wfp_profile_read", "wfp_debug_eta", "wfp_debug_taps", "wfp_debug_phi",
+           "wfp_profile", "wfp_profile_read", "wfp_local_noalloc", "wfp_debug_eta", "wfp_debug_taps", "wfp_debug_phi",
            "wfp_debug_soe"]
 
 
@@ -73,6 +73,8 @@ def lib():
     L.wfp_status_string.argtypes = [ctypes.c_int]
     L.wfp_status_string.restype = ctypes.c_char_p
     L.wfp_last_error.restype = ctypes.c_char_p
+    L.wfp_local_noalloc.argtypes = [_c_i64, vp, _c_i64, vp, vp, ctypes.c_int, _c_dbl, _c_dbl, _c_dbl, vp, vp]
+    L.wfp_local_noalloc.restype = ctypes.c_int
     L.wfp_profile.argtypes = [vp, ctypes.c_int]
     L.wfp_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), _pd,
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]
@@ -194,6 +196,18 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def local_noalloc(src_xy, tgt_xy, sigma_win, nmax: int, dt: float, band_limit: float, tol: float, out,
+                  stream: int | None = None):
+    """Local part of one step with no allocation (device tensors: src_xy (M,2), tgt_xy (Mt,2),
+    sigma_win (nmax, M), out (Mt,), all float64)."""
+    M = sigma_win.shape[1]
+    Mt = out.shape[0]
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    _check(lib().wfp_local_noalloc(M, p(src_xy), Mt, p(tgt_xy), p(sigma_win), int(nmax), dt, band_limit, tol,
+                                   p(out), ctypes.c_void_p(stream or 0)), "wfp_local_noalloc")
+    return out
 
 
 # ------------------------------------------------------------------ host-only diagnostics
