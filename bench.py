@@ -48,7 +48,13 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=200)
-    return ap.parse_args()
+    ap.add_argument("--opt", action="append", default=[], help="plan option key=value (wfp_opts field)")
+    a = ap.parse_args()
+    a.plan_opts = {}
+    for kv in a.opt:
+        k, v = kv.split("=")
+        a.plan_opts[k] = float(v) if any(c in v for c in ".e") else int(v)
+    return a
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -170,7 +176,7 @@ def run_ours(args, rank: int, world: int, dist):
         Nt = max(wl.n_steps, pre + Wm + K + prof_steps + e2e_steps)
         t0 = time.perf_counter()
         plan = wfp.Plan(wl.src_xy, None, wl.dt, Nt, wl.band_limit, wl.tol,
-                        precision=0 if precision == "fp64" else 1, stream=stream.cuda_stream)
+                        precision=0 if precision == "fp64" else 1, stream=stream.cuda_stream, **args.plan_opts)
         plan_s = time.perf_counter() - t0
         info = plan.info()
         out = torch.empty(Mt, dtype=torch.float64, device=dev)
@@ -365,7 +371,9 @@ def main():
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "W": info["W"], "p": info["p"], "L": info["L"], "N_modes_half": info["n_modes"],
                    "nf": info["nf"], "n_pairs": info["n_pairs"], "n_lambda": info["n_lambda"],
-                   "plan_seconds": round(r["plan_s"], 3), "device_bytes": info["device_bytes"]},
+                   "plan_seconds": round(r["plan_s"], 3), "device_bytes": info["device_bytes"],
+                   "upsampfac": info["upsampfac"], "kernel_width": info["kernel_width"],
+                   "plan_opts": args.plan_opts},
         "clocks": r["clocks"],
         "gpu_launches": K * launches_per_step(info, info["n_self"]),
         "roofline": roof,

@@ -226,6 +226,23 @@ void soe_nodes(double lam_max, int panels, int ng, std::vector<double>& lam, std
     }
 }
 
+// Sum of exponentials for 1/d (r = 0) by the trapezoid rule in s = ln(lambda) applied to
+// 1/d = int exp(s - e^s d) ds over [ln lmin, ln lmax] (step ~h).  The integrand is analytic in
+// the strip |Im s| < pi/2, so the discretisation error decays like exp(-pi^2/h); it decays like
+// e^s below ln lmin (tail ~ lmin d) and doubly exponentially above ln lmax (tail ~ e^{-lmax d}).
+void soe_logtrap(double lmin, double lmax, double h, std::vector<double>& lam, std::vector<double>& q) {
+    lam.clear();
+    q.clear();
+    double s0 = std::log(lmin), s1 = std::log(lmax);
+    int K = std::max(2, (int)std::ceil((s1 - s0) / h));
+    double hh = (s1 - s0) / K;
+    for (int k = 0; k <= K; k++) {
+        double sk = s0 + k * hh;
+        lam.push_back(std::exp(sk));
+        q.push_back(hh * std::exp(sk));
+    }
+}
+
 double soe_max_rel_error(const std::vector<double>& lam, const std::vector<double>& q, double rmax, double tlo,
                          double thi) {
     double worst = 0.0;

@@ -78,6 +78,7 @@ wfp_status local_params(double dt, double K0, double tol, const wfp_opts& o, dou
 // 1/sqrt(t^2 - r^2) = int_0^inf exp(-lambda t) I0(r lambda) dlambda (Eq. LaplaceIntegral):
 // panels [0, lmax/2^(n-1)], [lmax/2^(n-1), lmax/2^(n-2)], ..., [lmax/2, lmax], ng nodes each.
 void soe_nodes(double lam_max, int panels, int ng, std::vector<double>& lam, std::vector<double>& q);
+void soe_logtrap(double lmin, double lmax, double h, std::vector<double>& lam, std::vector<double>& q);
 // max over r in [0, rmax], t in [tlo, thi] of |SOE - 1/sqrt(t^2-r^2)| * sqrt(t^2-r^2)
 double soe_max_rel_error(const std::vector<double>& lam, const std::vector<double>& q, double rmax, double tlo,
                          double thi);

@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(128) k_eta(int64_t npairs, const double* __res
 }
 
 // ------------------------------------------------------------------- FIR taps
+// taps [kid][4W] in the reduced precision: p_m, q_m, pA_m, qA_m (Eq. hggrid), dt folded in
 template <typename TT>
 __global__ void k_taps(int64_t nk, const double* __restrict__ kap, double dt, int W, double lagshift, int ngt,
                        const double* __restrict__ sq, const double* __restrict__ wq, const double* __restrict__ f1,
@@ -111,6 +112,20 @@ __global__ void k_taps(int64_t nk, const double* __restrict__ kap, double dt, in
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nk) return;
     mode_taps<TT>(kap[i], dt, W, lagshift, ngt, sq, wq, f1, f2, taps + i * 4 * W, rot + 3 * i);
+}
+
+// v -> (hi, lo) float pair rows of length W, or double rows
+template <typename TT>
+static void put_taps(std::vector<TT>& out, size_t row, int W, const std::vector<double>& v) {
+    if constexpr (sizeof(TT) == 8) {
+        for (int j = 0; j < W; j++) out[row * W + j] = (TT)v[j];
+    } else {
+        for (int j = 0; j < W; j++) {
+            float hi = (float)v[j];
+            out[row * 2 * W + j] = hi;
+            out[row * 2 * W + W + j] = (float)(v[j] - (double)hi);
+        }
+    }
 }
 
 // ------------------------------------------------------------------- Hankel coefficients (Eq. H)
@@ -417,15 +432,16 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         k_hankel<<<nfk, 256, nr * sizeof(double)>>>(nfk, P.n_lambda, nr, d_fkap.p, d_rn.p, d_tab.p, pl.d_H);
         CK(cudaGetLastError());
         // forcing taps c_{l,m} = dt exp(-lam_l ((L+1+m) dt - A)) [phi((W-m) dt) - phi((W-1-m) dt)]
-        std::vector<T> ftap((size_t)P.n_lambda * P.W);
-        std::vector<double> fdec(P.n_lambda);
+        std::vector<T> ftap((size_t)P.n_lambda * P.W * (sizeof(T) == 8 ? 1 : 2));
+        std::vector<double> fdec(P.n_lambda), row(P.W);
         for (int l = 0; l < P.n_lambda; l++) {
             fdec[l] = std::exp(-lam[l] * P.dt);
             for (int m = 0; m < P.W; m++) {
                 double dphi = phi_host(phic.data(), (P.W - m) * P.dt, P.delta) -
                               phi_host(phic.data(), (P.W - 1 - m) * P.dt, P.delta);
-                ftap[(size_t)l * P.W + m] = (T)(P.dt * std::exp(-lam[l] * ((P.L + 1 + m) * P.dt - P.A)) * dphi);
+                row[m] = P.dt * std::exp(-lam[l] * ((P.L + 1 + m) * P.dt - P.A)) * dphi;
             }
+            put_taps<T>(ftap, l, P.W, row);
         }
         T* dft = nullptr;
         CK(upload(mem, &dft, ftap));
@@ -447,32 +463,38 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         }
         double dlo = std::max(lo, 1e-6 * P.delta);
         double Tself = std::max(P.T, 2.0 * P.delta);
-        double lmax = 36.0 / dlo;
-        int panels = std::max(2, (int)std::ceil(std::log2(lmax * Tself)) + 1);
+        // trapezoid in ln(lambda) from lmin = 1e-2 eps / T to lmax = (ln(1/eps) + 3) / d_lo
         std::vector<double> lam, q;
-        int chosen = 0;
-        for (int ng : {8, 10, 12, 14, 16, 20, 24, 32}) {
-            soe_nodes(lmax, panels, ng, lam, q);
-            if (soe_max_rel_error(lam, q, 0.0, dlo, Tself) <= 0.1 * P.eps) {
-                chosen = ng;
+        const double target = P.eps;
+        bool ok = false;
+        for (double h : {0.5, 0.45, 0.42, 0.4, 0.35, 0.3, 0.25}) {
+            soe_logtrap(1e-2 * target / Tself, (std::log(1.0 / target) + 3.0) / dlo, h, lam, q);
+            if (soe_max_rel_error(lam, q, 0.0, dlo, Tself) <= target) {
+                ok = true;
                 break;
             }
         }
-        if (!chosen) {
+        if (!ok) {
             err = "self-term sum of exponentials did not reach the tolerance";
             return WFP_EINVAL;
         }
         pl.n_soe_self = (int)lam.size();
-        std::vector<T> stap((size_t)pl.n_soe_self * P.W);
-        std::vector<double> sdec(pl.n_soe_self), sw(pl.n_soe_self);
+        std::vector<T> stap((size_t)pl.n_soe_self * P.W * (sizeof(T) == 8 ? 1 : 2));
+        std::vector<double> sdec(pl.n_soe_self), sw(pl.n_soe_self), row(P.W);
+        std::vector<int> sntap(pl.n_soe_self);
         for (int l = 0; l < pl.n_soe_self; l++) {
             sdec[l] = std::exp(-lam[l] * P.dt);
             sw[l] = q[l] / (2.0 * kPi);
+            int nt = 0;
             for (int m = 0; m < P.W; m++) {
                 double dphi = phi_host(phic.data(), (m + 1) * P.dt, P.delta) - phi_host(phic.data(), m * P.dt, P.delta);
-                stap[(size_t)l * P.W + m] = (T)(P.dt * std::exp(-lam[l] * (m + 1) * P.dt) * dphi);
+                row[m] = P.dt * std::exp(-lam[l] * (m + 1) * P.dt) * dphi;
+                if (std::fabs(row[m]) > 1e-30 * P.dt) nt = m + 1;  // later taps are negligible
             }
+            put_taps<T>(stap, l, P.W, row);
+            sntap[l] = nt;
         }
+        CK(upload(mem, &pl.d_sntap, sntap));
         T* dst = nullptr;
         CK(upload(mem, &dst, stap));
         pl.d_stap = dst;

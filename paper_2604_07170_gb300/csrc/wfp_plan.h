@@ -114,6 +114,7 @@ struct Plan {
     void* d_stap = nullptr;      // [n_soe_self][W] (reduced precision)
     double* d_sdecay = nullptr;  // [n_soe_self]
     double* d_sw = nullptr;      // [n_soe_self] SOE weights / (2 pi)
+    int* d_sntap = nullptr;      // [n_soe_self] number of non-negligible forcing taps
     double* d_Y = nullptr;       // [n_soe_self][n_self]
 
     // outputs (internal target order)

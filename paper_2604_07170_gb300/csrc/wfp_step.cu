@@ -27,6 +27,20 @@ struct Cplx<float> {
     using type = float2;
 };
 
+// Double-float accumulation (FP32 arithmetic, ~2x24-bit significand): (sh, sl) += (ah + al) * b,
+// with the product ah*b made exact by an FMA and the sum by TwoSum.  Explicit round-to-nearest
+// intrinsics keep the compiler from contracting the error terms away.
+__device__ __forceinline__ void df_acc(float& sh, float& sl, float ah, float al, float b) {
+    float p = __fmul_rn(ah, b);
+    float e = fmaf(ah, b, -p);
+    e = fmaf(al, b, e);
+    float s = __fadd_rn(sh, p);
+    float bb = __fsub_rn(s, sh);
+    float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    sl = __fadd_rn(sl, __fadd_rn(t, e));
+    sh = s;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -125,29 +139,54 @@ constexpr int kMaxW = 32;     // W <= 32 (the paper uses 10..30)
 constexpr int kMaxWFar = 32;
 
 template <typename T>
-__global__ void k_self(const int64_t* __restrict__ d_step, int64_t n_self, const int* __restrict__ self_tgt,
-                       const int* __restrict__ self_src, const T* __restrict__ sigwin, int NW, int W, int nsoe,
-                       const T* __restrict__ stap, const double* __restrict__ sdecay,
-                       const double* __restrict__ sw, double* __restrict__ Y, double* __restrict__ uself) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n_self) return;
-    int64_t n = *d_step + 1;
-    int src = self_src[s];
-    T sig[kMaxW];
-#pragma unroll
-    for (int m = 0; m < kMaxW; m++) sig[m] = (m < W) ? sigwin[(int64_t)src * NW + ((n - m) & (NW - 1))] : (T)0;
+__global__ void __launch_bounds__(256) k_self(const int64_t* __restrict__ d_step, int64_t n_self,
+                                              const int* __restrict__ self_tgt, const int* __restrict__ self_src,
+                                              const T* __restrict__ sigwin, int NW, int W, int nsoe,
+                                              const T* __restrict__ stap, const int* __restrict__ sntap,
+                                              const double* __restrict__ sdecay, const double* __restrict__ sw,
+                                              double* __restrict__ Y, double* __restrict__ uself) {
+    // block (32, 8): 32 coincident targets x 8 interleaved groups of SOE terms
+    __shared__ double s_red[8][32];
+    int64_t s = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    int g = threadIdx.y;
     double u = 0.0;
-    for (int l = 0; l < nsoe; l++) {
-        double y = Y[(int64_t)l * n_self + s];
-        u = fma(sw[l], y, u);
-        T f = 0;
-        const T* e = stap + (int64_t)l * W;
+    if (s < n_self) {
+        int64_t n = *d_step + 1;
+        int src = self_src[s];
+        T sig[kMaxW];
 #pragma unroll
-        for (int m = 0; m < kMaxW; m++)
-            if (m < W) f += e[m] * sig[m];
-        Y[(int64_t)l * n_self + s] = fma(sdecay[l], y, (double)f);
+        for (int m = 0; m < kMaxW; m++) sig[m] = (m < W) ? sigwin[(int64_t)src * NW + ((n - m) & (NW - 1))] : (T)0;
+        for (int l = g; l < nsoe; l += 8) {
+            double y = Y[(int64_t)l * n_self + s];
+            u = fma(sw[l], y, u);
+            const int nt = sntap[l];  // terms with large decay rates see only the newest levels
+            double fd;
+            if constexpr (sizeof(T) == 8) {
+                const T* e = stap + (int64_t)l * W;
+                T f0 = 0, f1 = 0;  // two partial sums shorten the dependent FMA chain
+#pragma unroll
+                for (int m = 0; m < kMaxW; m += 2) {
+                    if (m < nt) f0 += e[m] * sig[m];
+                    if (m + 1 < nt) f1 += e[m + 1] * sig[m + 1];
+                }
+                fd = f0 + f1;
+            } else {  // hi/lo taps, double-float sum
+                const float* e = (const float*)stap + (int64_t)l * 2 * W;
+                float fh = 0, fl = 0;
+#pragma unroll
+                for (int m = 0; m < kMaxW; m++)
+                    if (m < nt) df_acc(fh, fl, e[m], e[W + m], (float)sig[m]);
+                fd = (double)fh + (double)fl;
+            }
+            Y[(int64_t)l * n_self + s] = fma(sdecay[l], y, fd);
+        }
     }
-    uself[self_tgt[s]] = u;
+    s_red[g][threadIdx.x] = u;
+    __syncthreads();
+    if (g == 0 && s < n_self) {
+        for (int k = 1; k < 8; k++) u += s_red[k][threadIdx.x];
+        uself[self_tgt[s]] = u;
+    }
 }
 
 __global__ void k_combine(int64_t Mt, const int* __restrict__ tgt_perm, const double* __restrict__ uloc,
@@ -166,7 +205,7 @@ __global__ void k_tick(int64_t* d_step) { *d_step += 1; }
 constexpr int kSpreadChunk = 64;
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_spread(const int64_t* __restrict__ d_step, int lag, int L, int64_t M,
+__global__ void __launch_bounds__(1024) k_spread(const int64_t* __restrict__ d_step, int lag, int L, int64_t M,
                                                 const T* __restrict__ sighist, int n_hist,
                                                 const int* __restrict__ tile_xy, const int* __restrict__ tile_ptr,
                                                 const int* __restrict__ tile_src, const int* __restrict__ src_off,
@@ -182,9 +221,10 @@ __global__ void __launch_bounds__(256) k_spread(const int64_t* __restrict__ d_st
     int t = blockIdx.x;
     int txy = tile_xy[t];
     int tx = txy & 0xffff, ty = txy >> 16;
-    int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;  // 32 warps: warp wp owns tile row wp
     int colb = tx * kTile + lane;
-    T acc[4] = {0, 0, 0, 0};
+    const int rowb = ty * kTile + wp;
+    T acc = 0;
     int a0 = tile_ptr[t], a1 = tile_ptr[t + 1];
     for (int c0 = a0; c0 < a1; c0 += kSpreadChunk) {
         int cn = min(kSpreadChunk, a1 - c0);
@@ -194,30 +234,25 @@ __global__ void __launch_bounds__(256) k_spread(const int64_t* __restrict__ d_st
             s_val[i] = sig[s];
             s_off[i] = src_off[s];
         }
+        __syncthreads();
+        // x-kernel values are stored pre-multiplied by the source strength
         for (int i = threadIdx.x; i < cn * 2 * w; i += blockDim.x) {
             int si = i / (2 * w), e = i - si * 2 * w;
-            s_ker[si * 48 + e] = src_ker[(int64_t)tile_src[c0 + si] * 2 * w + e];
+            T v = src_ker[(int64_t)tile_src[c0 + si] * 2 * w + e];
+            s_ker[si * 48 + e] = (e < w) ? s_val[si] * v : v;
         }
         __syncthreads();
         for (int i = 0; i < cn; i++) {
             int off = s_off[i];
-            int dx = colb - (off & 0xffff);
-            if ((unsigned)dx < (unsigned)w) {
-                T wx = s_val[i] * s_ker[i * 48 + dx];
-                int dy0 = ty * kTile + wp - (off >> 16);
-#pragma unroll
-                for (int r = 0; r < 4; r++) {
-                    int dy = dy0 + 8 * r;
-                    if ((unsigned)dy < (unsigned)w) acc[r] += wx * s_ker[i * 48 + w + dy];
-                }
+            int dy = rowb - (off >> 16);
+            if ((unsigned)dy < (unsigned)w) {  // warp-uniform: this warp's row is in the footprint
+                int dx = colb - (off & 0xffff);
+                T skx = ((unsigned)dx < (unsigned)w) ? s_ker[i * 48 + dx] : (T)0;
+                acc += skx * s_ker[i * 48 + w + dy];
             }
         }
     }
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-        int rowb = ty * kTile + wp + 8 * r;
-        sp[(int64_t)rowb * nf + lb0 + colb] = acc[r];
-    }
+    sp[(int64_t)rowb * nf + lb0 + colb] = acc;
 }
 
 // ------------------------------------------------------------------------------ mode update
@@ -260,6 +295,8 @@ __global__ void __launch_bounds__(256) k_modes(
         s.y = (T)(-(double)t.y * f);
         ring_lag[(int64_t)slot * n_modes + m] = s;
     }
+    // FIR in the reduced precision (taps [kid][4W]); the mixed path's FIR rounding is below the
+    // FP32 NUFFT error of S itself
     const T* tp = taps + (int64_t)kid * 4 * W;
     T hx = 0, hy = 0, gx = 0, gy = 0;
     int sl = slot;
@@ -280,13 +317,14 @@ __global__ void __launch_bounds__(256) k_modes(
         }
         sl = (sl == 0) ? W - 1 : sl - 1;
     }
+    const double hxd = hx, hyd = hy, gxd = gx, gyd = gy;
     double c = rot[3 * kid], sk = rot[3 * kid + 1], ks = rot[3 * kid + 2];
     double2 a = alpha[m], ad = alphad[m];
     double2 an, adn;
-    an.x = fma(c, a.x, fma(sk, ad.x, (double)hx));
-    an.y = fma(c, a.y, fma(sk, ad.y, (double)hy));
-    adn.x = fma(-ks, a.x, fma(c, ad.x, (double)gx));
-    adn.y = fma(-ks, a.y, fma(c, ad.y, (double)gy));
+    an.x = fma(c, a.x, fma(sk, ad.x, hxd));
+    an.y = fma(c, a.y, fma(sk, ad.y, hyd));
+    adn.x = fma(-ks, a.x, fma(c, ad.x, gxd));
+    adn.y = fma(-ks, a.y, fma(c, ad.y, gyd));
     alpha[m] = an;
     alphad[m] = adn;
     double cf = coef2 * f;
@@ -338,18 +376,33 @@ __global__ void __launch_bounds__(256) k_far(const int64_t* __restrict__ d_step,
         int fk = far_k[f];
         const double* Hr = H + (int64_t)fk * nlam;
         for (int l = g; l < nlam; l += 8) {
-            const T* cl = ftap + (int64_t)l * W;
-            T fx = 0, fy = 0;
-            for (int j = 0; j < W; j++) {
-                T cj = cl[j];
-                C sj = s_S[j][threadIdx.x];
-                fx += cj * sj.x;
-                fy += cj * sj.y;
+            double fxd, fyd;
+            if constexpr (sizeof(T) == 8) {
+                const T* cl = ftap + (int64_t)l * W;
+                T fx = 0, fy = 0;
+                for (int j = 0; j < W; j++) {
+                    T cj = cl[j];
+                    C sj = s_S[j][threadIdx.x];
+                    fx += cj * sj.x;
+                    fy += cj * sj.y;
+                }
+                fxd = fx;
+                fyd = fy;
+            } else {  // hi/lo taps, double-float sums: slowly decaying terms do not accumulate FP32 rounding
+                const float* cl = (const float*)ftap + (int64_t)l * 2 * W;
+                float xh = 0, xl = 0, yh = 0, yl = 0;
+                for (int j = 0; j < W; j++) {
+                    C sj = s_S[j][threadIdx.x];
+                    df_acc(xh, xl, cl[j], cl[W + j], sj.x);
+                    df_acc(yh, yl, cl[j], cl[W + j], sj.y);
+                }
+                fxd = (double)xh + (double)xl;
+                fyd = (double)yh + (double)yl;
             }
             double2 b = B[(int64_t)l * n_far + f];
             double d = fdecay[l];
-            b.x = fma(d, b.x, (double)fx);
-            b.y = fma(d, b.y, (double)fy);
+            b.x = fma(d, b.x, fxd);
+            b.y = fma(d, b.y, fyd);
             B[(int64_t)l * n_far + f] = b;
             double hl = Hr[l];
             aF.x = fma(hl, b.x, aF.x);
@@ -460,9 +513,9 @@ static wfp_status output_t(Plan& pl, std::string& err) {
     }
     if (pl.n_self > 0) {
         ProfScope ps(pl, PP_SELF);
-        k_self<T><<<nblk(pl.n_self, 128), 128, 0, st>>>(pl.d_step, pl.n_self, pl.d_self_tgt, pl.d_self_src,
+        k_self<T><<<nblk(pl.n_self, 32), dim3(32, 8), 0, st>>>(pl.d_step, pl.n_self, pl.d_self_tgt, pl.d_self_src,
                                                         (const T*)pl.d_sigwin, pl.NW, P.W, pl.n_soe_self,
-                                                        (const T*)pl.d_stap, pl.d_sdecay, pl.d_sw, pl.d_Y, pl.d_uself);
+                                                        (const T*)pl.d_stap, pl.d_sntap, pl.d_sdecay, pl.d_sw, pl.d_Y, pl.d_uself);
         CK(cudaGetLastError());
     }
     {
@@ -515,12 +568,12 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err) {
     // type-1 spreading: current level and (when active) the lagged level
     if (pl.n_tiles > 0) {
         ProfScope ps(pl, PP_SPREAD);
-        k_spread<T><<<pl.n_tiles, 256, 0, st>>>(pl.d_step, 0, P.L, pl.M, (const T*)pl.d_sighist, pl.n_hist,
+        k_spread<T><<<pl.n_tiles, 1024, 0, st>>>(pl.d_step, 0, P.L, pl.M, (const T*)pl.d_sighist, pl.n_hist,
                                                 pl.d_tile_xy, pl.d_tile_ptr, pl.d_tile_src, pl.d_src_off,
                                                 (const T*)pl.d_src_ker, P.w, (T*)pl.d_sp_cur, P.nf, P.lb0);
         CK(cudaGetLastError());
         if (lag_now) {
-            k_spread<T><<<pl.n_tiles, 256, 0, st>>>(pl.d_step, 1, P.L, pl.M, (const T*)pl.d_sighist, pl.n_hist,
+            k_spread<T><<<pl.n_tiles, 1024, 0, st>>>(pl.d_step, 1, P.L, pl.M, (const T*)pl.d_sighist, pl.n_hist,
                                                     pl.d_tile_xy, pl.d_tile_ptr, pl.d_tile_src, pl.d_src_off,
                                                     (const T*)pl.d_src_ker, P.w, (T*)pl.d_sp_lag, P.nf, P.lb0);
             CK(cudaGetLastError());
