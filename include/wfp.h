@@ -67,6 +67,11 @@ enum { WFP_FP64 = 0, WFP_MIXED = 1 };
  *                 domain size) the self term is excluded, as in Eq. exactSol.
  *   stream        cudaStream_t to run on, or NULL for a plan-owned stream.
  *   use_graph     1 (default): the per-step device work is captured once into a CUDA graph.
+ *   lag_mode      how S(k, t - A+ + delta) reaches the removal term of Eq. hggrid:
+ *                 WFP_LAG_RECOMPUTE recomputes it each step by a second (lagged) type-1 NUFFT of
+ *                 the stored signal history, as the paper does (Sec. 4.3); WFP_LAG_STORE keeps the
+ *                 last L + W levels of S per mode in device memory; WFP_LAG_AUTO (0, default) stores
+ *                 when that history takes at most 40% of the free device memory, else recomputes.
  */
 typedef struct {
     int precision;
@@ -80,7 +85,10 @@ typedef struct {
     int exclude_self;
     void* stream;
     int use_graph;
+    int lag_mode;
 } wfp_opts;
+
+enum { WFP_LAG_AUTO = 0, WFP_LAG_RECOMPUTE = 1, WFP_LAG_STORE = 2 };
 
 /*
  * Derived parameters of a plan (normalised units: the bounding square of all points is
@@ -106,6 +114,8 @@ typedef struct {
     int lag_active, far_active;
     int precision;
     int64_t device_bytes;            /* device memory held by the plan */
+    int lag_store;                   /* 1: S history stored (L + W levels), 0: lagged NUFFT */
+    int64_t s_levels;                /* levels of S kept per mode */
 } wfp_info;
 
 typedef struct wfp_plan_s* wfp_plan;

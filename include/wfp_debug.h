@@ -42,6 +42,15 @@ wfp_status wfp_debug_phi(double t, double delta, double eps, double* phi, double
  */
 wfp_status wfp_debug_soe(double lam_max, int panels, int ng, double* lam, double* q);
 
+/*
+ * Hankel coefficients of the far history (Sec. 5, Eq. H) at wavenumber magnitude kappa:
+ * H_l = q_l exp(-A lam_l) int_0^A J0(kappa r) I0(lam_l r) phi_Delta(A - r) r dr for the dyadic
+ * sum of exponentials (lam_max, panels, ng) above, with the composite Gauss-Legendre rule in r
+ * that plans use.  H: panels*ng doubles.
+ */
+wfp_status wfp_debug_hankel(double kappa, double A, double Delta, double eps, double lam_max, int panels, int ng,
+                            double* H);
+
 #ifdef __cplusplus
 }
 #endif

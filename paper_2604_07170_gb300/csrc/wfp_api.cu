@@ -263,6 +263,8 @@ wfp_status wfp_plan_get_info(wfp_plan plan, wfp_info* info) {
     info->n_pairs = pl.n_pairs;
     info->n_self = pl.n_self;
     info->device_bytes = pl.mem.bytes;
+    info->lag_store = pl.lag_store;
+    info->s_levels = pl.R_cur;
     return WFP_OK;
 }
 
@@ -369,6 +371,33 @@ wfp_status wfp_debug_phi(double t, double delta, double eps, double* phi, double
     if (phi) *phi = phi_host(phic.data(), t, delta);
     if (dphi) *dphi = dphi_host(t, delta, b);
     if (d2phi) *d2phi = d2phi_host(t, delta, b);
+    return WFP_OK;
+}
+
+wfp_status wfp_debug_hankel(double kappa, double A, double Delta, double eps, double lam_max, int panels, int ng,
+                            double* H) {
+    if (!H || panels < 1 || panels > 64 || ng < 1 || ng > 64 || !(A > Delta) || !(Delta > 0))
+        return fail(WFP_EINVAL, "bad argument");
+    std::vector<double> lam, q, phic;
+    soe_nodes(lam_max, panels, ng, lam, q);
+    build_phi_table(std::log(1.0 / eps), phic);
+    // same composite rule as the plan: 32 panels x 16 Gauss-Legendre nodes on [0, A]
+    const int npan = 32, ngr = 16;
+    double gx[ngr], gw[ngr];
+    gauss_legendre(ngr, gx, gw);
+    for (size_t l = 0; l < lam.size(); l++) {
+        double acc = 0.0;
+        for (int k = 0; k < npan; k++)
+            for (int i = 0; i < ngr; i++) {
+                double a = A * k / npan, b = A * (k + 1) / npan;
+                double r = 0.5 * (b - a) * gx[i] + 0.5 * (b + a), wr = 0.5 * (b - a) * gw[i];
+                double x = A - r;
+                double ph = (x <= 0.0) ? 0.0 : (x >= Delta ? 1.0 : cheb_phi(phic.data(), 2.0 * x / Delta - 1.0));
+                acc += wr * std::cyl_bessel_j(0.0, kappa * r) * std::cyl_bessel_i(0.0, lam[l] * r) *
+                       std::exp(-lam[l] * A) * ph * r;
+            }
+        H[l] = q[l] * acc;
+    }
     return WFP_OK;
 }
 

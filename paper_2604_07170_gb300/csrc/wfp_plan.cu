@@ -554,6 +554,28 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(upload(mem, &pl.d_tile_src, tsrc));
     }
 
+    // ---- lagged S: stored history (L + W levels per mode) or a lagged type-1 NUFFT (Sec. 4.3)
+    {
+        size_t hist = (size_t)(P.L + P.W) * pl.n_modes * sizeof(C);
+        size_t freeb = 0, totb = 0;
+        CK(cudaMemGetInfo(&freeb, &totb));
+        int mode = pl.opts.lag_mode;
+        if (mode != WFP_LAG_AUTO && mode != WFP_LAG_RECOMPUTE && mode != WFP_LAG_STORE) {
+            err = "lag_mode must be WFP_LAG_AUTO, WFP_LAG_RECOMPUTE or WFP_LAG_STORE";
+            return WFP_EINVAL;
+        }
+        pl.lag_store = P.lag_active && (mode == WFP_LAG_STORE || (mode == WFP_LAG_AUTO && hist <= 0.4 * freeb));
+        if (pl.lag_store) {
+            pl.R_cur = P.L + P.W;
+            pl.R_lag = pl.R_cur;
+            pl.lag_off = 0;
+        } else {
+            pl.R_cur = P.W;
+            pl.R_lag = P.W;
+            pl.lag_off = P.L;
+        }
+    }
+
     // ---- grids and cuFFT plans (two-stage pruned transforms)
     {
         const int64_t nf = P.nf, nh2 = P.nf / 2 + 1, nc1 = P.Nh + 1;
@@ -566,7 +588,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         pl.d_tb_cur = tb;
         CK(mem.alloc(&tc, (size_t)nf * nc1));
         pl.d_tc_cur = tc;
-        if (P.lag_active) {
+        if (P.lag_active && !pl.lag_store) {
             CK(mem.alloc(&sp, (size_t)P.nb * nf));
             pl.d_sp_lag = sp;
             CK(mem.alloc(&tb, (size_t)nf * nh2));
@@ -606,20 +628,20 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         T* w = nullptr;
         CK(mem.alloc(&w, (size_t)M * pl.NW));
         pl.d_sigwin = w;
-        pl.n_hist = P.lag_active ? P.L + 1 : 1;
+        pl.n_hist = (P.lag_active && !pl.lag_store) ? P.L + 1 : 1;
         CK(mem.alloc(&w, (size_t)pl.n_hist * M));
         pl.d_sighist = w;
         CK(mem.alloc(&pl.d_sig_in, M));
         CK(mem.alloc(&pl.d_alpha, pl.n_modes));
         CK(mem.alloc(&pl.d_alphad, pl.n_modes));
         C* r = nullptr;
-        CK(mem.alloc(&r, (size_t)P.W * pl.n_modes));
+        CK(mem.alloc(&r, (size_t)pl.R_cur * pl.n_modes));
         pl.d_ring = r;
-        if (P.lag_active) {
-            CK(mem.alloc(&r, (size_t)P.W * pl.n_modes));
+        if (P.lag_active && !pl.lag_store) {
+            CK(mem.alloc(&r, (size_t)pl.R_lag * pl.n_modes));
             pl.d_ring_lag = r;
         } else {
-            pl.d_ring_lag = pl.d_ring;  // never read while the lag is inactive
+            pl.d_ring_lag = pl.d_ring;  // the stored history serves both FIRs (or the lag is inactive)
         }
         CK(mem.alloc(&pl.d_uloc, Mt));
         CK(mem.alloc(&pl.d_uh, Mt));

@@ -94,8 +94,10 @@ struct Plan {
     double* d_rot = nullptr;     // [n_kappa][3] cos(k dt), sin(k dt)/k, k sin(k dt)
     double2* d_alpha = nullptr;  // [n_modes]
     double2* d_alphad = nullptr; // [n_modes]
-    void* d_ring = nullptr;      // [W][n_modes] S at the last W levels (complex, ring precision)
-    void* d_ring_lag = nullptr;  // [W][n_modes] S at the last W lagged levels
+    void* d_ring = nullptr;      // [R_cur][n_modes] S by level: level l in slot l mod R_cur
+    void* d_ring_lag = nullptr;  // [R_lag][n_modes] lagged S: level l in slot (l + lag_off) mod R_lag
+    bool lag_store = false;      // S history kept (R_cur = L + W, ring_lag = ring) instead of a lagged NUFFT
+    int R_cur = 0, R_lag = 0, lag_off = 0;
 
     // far history (Sec. 5)
     int64_t n_far = 0, n_fkappa = 0;

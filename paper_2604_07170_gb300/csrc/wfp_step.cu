@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <cufft.h>
 
+#include <cmath>
+
 #include "wfp_plan.h"
 
 namespace wfp {
@@ -267,9 +269,10 @@ __global__ void __launch_bounds__(256) k_modes(
     const int64_t* __restrict__ d_step, int64_t n_modes, int W, int L, int Nh, int nf, const int2* __restrict__ mode_n,
     const int* __restrict__ mode_k, const double* __restrict__ fac, double coef2,
     const typename Cplx<T>::type* __restrict__ tc_cur, const typename Cplx<T>::type* __restrict__ tc_lag,
-    typename Cplx<T>::type* __restrict__ ring, typename Cplx<T>::type* __restrict__ ring_lag,
+    typename Cplx<T>::type* __restrict__ ring, typename Cplx<T>::type* __restrict__ ring_lag, int R_cur, int R_lag,
+    int lag_off, int write_lag,
     const T* __restrict__ taps, const double* __restrict__ rot, double2* __restrict__ alpha,
-    double2* __restrict__ alphad, typename Cplx<T>::type* __restrict__ td) {
+    double2* __restrict__ alphad, typename Cplx<T>::type* __restrict__ td, int64_t near_sq) {
     using C = typename Cplx<T>::type;
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n_modes) return;
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(256) k_modes(
     int row = nn.x < 0 ? nn.x + nf : nn.x;
     int64_t gi = (int64_t)row * (Nh + 1) + nn.y;
     double f = fac[nn.x < 0 ? -nn.x : nn.x] * fac[nn.y];
-    int slot = (int)(n % W);
+    const int slot = (int)(n % R_cur);
     {
         C t = tc_cur[gi];
         C s;
@@ -288,18 +291,29 @@ __global__ void __launch_bounds__(256) k_modes(
         s.y = (T)(-(double)t.y * f);
         ring[(int64_t)slot * n_modes + m] = s;
     }
-    if (lag) {
+    if (lag && write_lag) {  // lagged NUFFT result: level n - L goes to slot (n - L + lag_off) mod R_lag
         C t = tc_lag[gi];
         C s;
         s.x = (T)((double)t.x * f);
         s.y = (T)(-(double)t.y * f);
-        ring_lag[(int64_t)slot * n_modes + m] = s;
+        ring_lag[(int64_t)((n - L + lag_off) % R_lag) * n_modes + m] = s;
     }
     // FIR in the reduced precision (taps [kid][4W]); the mixed path's FIR rounding is below the
     // FP32 NUFFT error of S itself
+    // the near history is truncated at |k| <= K (Eq. uhtraptrunc); modes between K and the far
+    // cut-off carry only S (for the far forcing) and the far coefficient added by k_far
+    if ((int64_t)nn.x * nn.x + (int64_t)nn.y * nn.y > near_sq) {
+        C o;
+        o.x = 0;
+        o.y = 0;
+        td[gi] = o;
+        if (nn.y == 0 && nn.x > 0) td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
+        return;
+    }
     const T* tp = taps + (int64_t)kid * 4 * W;
     T hx = 0, hy = 0, gx = 0, gy = 0;
-    int sl = slot;
+    int sl = slot;                                                      // level n - j
+    int sll = (int)((((n - L + lag_off) % R_lag) + R_lag) % R_lag);     // level n - L - j
     for (int j = 0; j < W; j++) {
         C a = ring[(int64_t)sl * n_modes + m];
         T p = tp[j], q = tp[W + j];
@@ -308,14 +322,15 @@ __global__ void __launch_bounds__(256) k_modes(
         gx += q * a.x;
         gy += q * a.y;
         if (lag) {
-            C b = ring_lag[(int64_t)sl * n_modes + m];
+            C b = ring_lag[(int64_t)sll * n_modes + m];
             T pa = tp[2 * W + j], qa = tp[3 * W + j];
             hx -= pa * b.x;
             hy -= pa * b.y;
             gx -= qa * b.x;
             gy -= qa * b.y;
         }
-        sl = (sl == 0) ? W - 1 : sl - 1;
+        sl = (sl == 0) ? R_cur - 1 : sl - 1;
+        sll = (sll == 0) ? R_lag - 1 : sll - 1;
     }
     const double hxd = hx, hyd = hy, gxd = gx, gyd = gy;
     double c = rot[3 * kid], sk = rot[3 * kid + 1], ks = rot[3 * kid + 2];
@@ -349,8 +364,8 @@ __global__ void __launch_bounds__(256) k_far(const int64_t* __restrict__ d_step,
                                              int L, int Nh, int nf, int nlam, const int* __restrict__ far_mode,
                                              const int* __restrict__ far_k, const int2* __restrict__ mode_n,
                                              const double* __restrict__ fac, double coef2,
-                                             const typename Cplx<T>::type* __restrict__ ring_lag,
-                                             const double* __restrict__ H, const T* __restrict__ ftap,
+                                             const typename Cplx<T>::type* __restrict__ ring_lag, int R_lag,
+                                             int lag_off, const double* __restrict__ H, const T* __restrict__ ftap,
                                              const double* __restrict__ fdecay, double2* __restrict__ B,
                                              typename Cplx<T>::type* __restrict__ td) {
     using C = typename Cplx<T>::type;
@@ -364,7 +379,7 @@ __global__ void __launch_bounds__(256) k_far(const int64_t* __restrict__ d_step,
     int64_t m = valid ? far_mode[f] : 0;
     // stage the W lagged levels S_{n-L-j} of this block's 32 modes
     for (int j = g; j < W; j += 8) {
-        int sl = (int)(((n - j) % W + W) % W);
+        int sl = (int)((((n - L - j + lag_off) % R_lag) + R_lag) % R_lag);  // level n - L - j
         C z;
         z.x = 0;
         z.y = 0;
@@ -572,7 +587,7 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err) {
                                                 pl.d_tile_xy, pl.d_tile_ptr, pl.d_tile_src, pl.d_src_off,
                                                 (const T*)pl.d_src_ker, P.w, (T*)pl.d_sp_cur, P.nf, P.lb0);
         CK(cudaGetLastError());
-        if (lag_now) {
+        if (lag_now && !pl.lag_store) {
             k_spread<T><<<pl.n_tiles, 1024, 0, st>>>(pl.d_step, 1, P.L, pl.M, (const T*)pl.d_sighist, pl.n_hist,
                                                     pl.d_tile_xy, pl.d_tile_ptr, pl.d_tile_src, pl.d_src_off,
                                                     (const T*)pl.d_src_ker, P.w, (T*)pl.d_sp_lag, P.nf, P.lb0);
@@ -589,7 +604,7 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err) {
         err = "cufft type-1 column pass failed";
         return WFP_ECUDA;
     }
-    if (lag_now) {
+    if (lag_now && !pl.lag_store) {
         if (exec_r2c<T>(pl.fftA, (T*)pl.d_sp_lag, (C*)pl.d_tb_lag + (int64_t)P.lb0 * nh2) != WFP_OK ||
             exec_c2c<T>(pl.fftB, (C*)pl.d_tb_lag, (C*)pl.d_tc_lag, CUFFT_FORWARD) != WFP_OK) {
             err = "cufft lagged type-1 failed";
@@ -601,8 +616,9 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err) {
     ProfScope psm(pl, PP_MODES);
     k_modes<T><<<nblk(pl.n_modes, 256), 256, 0, st>>>(
         pl.d_step, pl.n_modes, P.W, P.L, P.Nh, P.nf, pl.d_mode_n, pl.d_mode_k, pl.d_fac, coef2, (const C*)pl.d_tc_cur,
-        (const C*)pl.d_tc_lag, (C*)pl.d_ring, (C*)pl.d_ring_lag, (const T*)pl.d_taps, pl.d_rot, pl.d_alpha,
-        pl.d_alphad, (C*)pl.d_td);
+        (const C*)pl.d_tc_lag, (C*)pl.d_ring, (C*)pl.d_ring_lag, pl.R_cur, pl.R_lag, pl.lag_off, pl.lag_store ? 0 : 1,
+        (const T*)pl.d_taps, pl.d_rot, pl.d_alpha,
+        pl.d_alphad, (C*)pl.d_td, (int64_t)std::floor((P.K / P.dk) * (P.K / P.dk)));
     CK(cudaGetLastError());
     psm.stop();
     if (lag_now && P.far_active && pl.n_far > 0) {
@@ -610,7 +626,7 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err) {
         dim3 blk(32, 8);
         k_far<T><<<nblk(pl.n_far, 32), blk, 0, st>>>(pl.d_step, pl.n_far, pl.n_modes, P.W, P.L, P.Nh, P.nf,
                                                       P.n_lambda, pl.d_far_mode, pl.d_far_k, pl.d_mode_n, pl.d_fac,
-                                                      coef2, (const C*)pl.d_ring_lag, pl.d_H, (const T*)pl.d_ftap, pl.d_fdecay,
+                                                      coef2, (const C*)pl.d_ring_lag, pl.R_lag, pl.lag_off, pl.d_H, (const T*)pl.d_ftap, pl.d_fdecay,
                                                       pl.d_B, (C*)pl.d_td);
         CK(cudaGetLastError());
     }

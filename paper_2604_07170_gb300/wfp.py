@@ -15,6 +15,7 @@ from . import build as _build
 
 WFP_OK, WFP_EINVAL, WFP_ENOMEM, WFP_ECUDA, WFP_ESTATE, WFP_ETIMEOUT, WFP_EUNSUPPORTED = range(7)
 FP64, MIXED = 0, 1
+LAG_AUTO, LAG_RECOMPUTE, LAG_STORE = 0, 1, 2
 
 _c_i64 = ctypes.c_int64
 _c_dbl = ctypes.c_double
@@ -25,7 +26,7 @@ class wfp_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("eps", _c_dbl), ("W", ctypes.c_int), ("p", ctypes.c_int),
                 ("Kf", _c_dbl), ("upsampfac", _c_dbl), ("kernel_width", ctypes.c_int),
                 ("soe_nodes", ctypes.c_int), ("exclude_self", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("lag_mode", ctypes.c_int)]
 
 
 class wfp_info(ctypes.Structure):
@@ -37,7 +38,8 @@ class wfp_info(ctypes.Structure):
                 ("soe_panels", ctypes.c_int), ("soe_nodes", ctypes.c_int), ("n_self_soe", ctypes.c_int),
                 ("nf", ctypes.c_int), ("nb", ctypes.c_int), ("kernel_width", ctypes.c_int),
                 ("upsampfac", _c_dbl), ("n_pairs", _c_i64), ("n_self", _c_i64), ("lag_active", ctypes.c_int),
-                ("far_active", ctypes.c_int), ("precision", ctypes.c_int), ("device_bytes", _c_i64)]
+                ("far_active", ctypes.c_int), ("precision", ctypes.c_int), ("device_bytes", _c_i64),
+                ("lag_store", ctypes.c_int), ("s_levels", _c_i64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -49,7 +51,7 @@ _lib = None
 EXPORTS = ["wfp_opts_default", "wfp_plan_create", "wfp_step", "wfp_destroy", "wfp_plan_get_info",
            "wfp_step_components", "wfp_select_params", "wfp_status_string", "wfp_last_error",
            "wfp_profile", "wfp_profile_read", "wfp_local_noalloc", "wfp_debug_eta", "wfp_debug_taps", "wfp_debug_phi",
-           "wfp_debug_soe"]
+           "wfp_debug_soe", "wfp_debug_hankel"]
 
 
 def lib():
@@ -82,6 +84,8 @@ def lib():
     L.wfp_debug_taps.argtypes = [_c_dbl, _c_dbl, ctypes.c_int, _c_dbl, _c_dbl, _pd, _pd]
     L.wfp_debug_phi.argtypes = [_c_dbl, _c_dbl, _c_dbl, _pd, _pd, _pd]
     L.wfp_debug_soe.argtypes = [_c_dbl, ctypes.c_int, ctypes.c_int, _pd, _pd]
+    L.wfp_debug_hankel.argtypes = [_c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_dbl, ctypes.c_int, ctypes.c_int, _pd]
+    L.wfp_debug_hankel.restype = ctypes.c_int
     for name in ("wfp_plan_create", "wfp_step", "wfp_destroy", "wfp_plan_get_info", "wfp_step_components",
                  "wfp_profile", "wfp_profile_read",
                  "wfp_select_params", "wfp_debug_eta", "wfp_debug_taps", "wfp_debug_phi", "wfp_debug_soe"):
@@ -227,6 +231,12 @@ def debug_phi(t, delta, eps):
     a, b, c = _c_dbl(), _c_dbl(), _c_dbl()
     _check(lib().wfp_debug_phi(t, delta, eps, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "wfp_debug_phi")
     return a.value, b.value, c.value
+
+
+def debug_hankel(kappa, A, Delta, eps, lam_max=36.0, panels=20, ng=32) -> np.ndarray:
+    H = np.zeros(panels * ng)
+    _check(lib().wfp_debug_hankel(kappa, A, Delta, eps, lam_max, panels, ng, _dptr(H)), "wfp_debug_hankel")
+    return H
 
 
 def debug_soe(lam_max, panels, ng):
