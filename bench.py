@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--opt", action="append", default=[], help="plan option key=value (wfp_opts field)")
+    ap.add_argument("--drive", type=int, default=0,
+                    help="only step the workload this many times with graphs off and exit (profiler target)")
+    ap.add_argument("--serve", type=int, default=0,
+                    help="serving benchmark with this many requests (Poisson arrivals) instead of the step loop")
+    ap.add_argument("--serve-load", type=float, default=0.8, help="offered load as a fraction of batch capacity")
+    ap.add_argument("--max-active", type=int, default=48)
     a = ap.parse_args()
     a.plan_opts = {}
     for kv in a.opt:
@@ -332,8 +338,95 @@ def launches_per_step(info: dict, n_self: int) -> int:
     return 1 + 1 + (1 if n_self > 0 else 0) + 1 + 2 + 1 + (1 if info["far_active"] else 0) + 1 + 1
 
 
+def drive(args):
+    """Step the workload `args.drive` times through the C ABI with host buffers, graphs off, so that a
+    profiler sees every kernel as its own launch.  Prints nothing but a completion line."""
+    from paper_2604_07170_gb300 import inputs, wfp
+    wl = inputs.make(args.config)
+    opts = dict(args.plan_opts)
+    opts.setdefault("use_graph", 0)
+    plan = wfp.Plan(wl.src_xy, None, wl.dt, max(wl.n_steps, args.drive), wl.band_limit, wl.tol,
+                    precision=0 if args.precision == "fp64" else 1, **opts)
+    u = np.empty(wl.M)
+    for n0 in range(0, args.drive, 256):
+        sig = wl.sigma(n0 + 1, min(args.drive, n0 + 256) + 1)
+        for k in range(sig.shape[0]):
+            plan.step(sig[k], u)
+    plan.close()
+    print(f"drove {args.drive} steps of {args.config} ({args.precision})")
+
+
+def serve(args):
+    """Request-server benchmark: a closed batch of all requests (capacity), then the same requests
+    arriving as a Poisson stream at a fraction of that capacity (latency percentiles)."""
+    import torch
+    from paper_2604_07170_gb300 import inputs, wfp
+    reqs = inputs.serve_requests(args.serve)
+    work = np.array([w.M * w.n_steps for w in reqs], dtype=np.float64)
+    torch.cuda.init()
+    free_b, _ = torch.cuda.mem_get_info()
+    budget = int(0.85 * free_b)
+    prec = 0 if args.precision == "fp64" else 1
+
+    def run(arrivals):
+        sv = wfp.Server(budget, args.max_active, precision=prec, **args.plan_opts)
+        ids = [None] * len(reqs)
+        t0 = time.perf_counter()
+        nxt = 0
+        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            while True:
+                now = time.perf_counter() - t0
+                while nxt < len(reqs) and arrivals[nxt] <= now:
+                    w = reqs[nxt]
+                    ids[nxt] = sv.submit(w.src_xy, w.params, w.dt, w.n_steps, w.band_limit, w.tol)
+                    nxt += 1
+                a, p = sv.tick()
+                if a == 0 and p == 0:
+                    if nxt == len(reqs):
+                        break
+                    time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+        st = [sv.query(i) for i in ids]
+        sv.close()
+        bad = [i for i, q in enumerate(st) if q["state"] != wfp.REQ_DONE]
+        if bad:
+            raise RuntimeError(f"requests failed: {bad}")
+        lat = np.array([q["t_done"] - q["t_submit"] for q in st])
+        wait = np.array([q["t_admit"] - q["t_submit"] for q in st])
+        span = max(q["t_done"] for q in st) - min(q["t_submit"] for q in st)
+        return lat, wait, span, clk.summary()
+
+    lat_b, _, span_b, _ = run(np.zeros(len(reqs)))
+    cap = work.sum() / span_b
+    lam = args.serve_load * cap / work.mean()
+    rng = np.random.default_rng(inputs.SEED0 + 5)
+    arr = np.cumsum(rng.exponential(1.0 / lam, len(reqs)))
+    arr -= arr[0]
+    lat, wait, span, clocks = run(arr)
+    line = {
+        "metric": "serving target-updates/s and request latency (Poisson arrivals)",
+        "value": work.sum() / span, "unit": "target-updates/s", "n_gpus": 1, "steps": len(reqs), "warmup": 0,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == 0 else "f64-state/f32",
+        "data": "synthetic request mix (seeded ellipse geometry, Gaussian-sinusoid signals generated on the device)",
+        "config": {"workload": f"{len(reqs)} requests: M log-uniform 1e3..1e5, N_t uniform 500..4000, box 10..100, "
+                               f"tol 1e-6, {args.precision}",
+                   "arrival_rate_per_s": lam, "offered_load": args.serve_load, "hbm_budget_bytes": budget,
+                   "max_active": args.max_active},
+        "batch_capacity": {"value": cap, "unit": "target-updates/s", "makespan_s": span_b},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "max": float(lat.max())},
+        "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+        "makespan_s": span, "clocks": clocks,
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
+    if args.drive:
+        return drive(args)
+    if args.serve:
+        return serve(args)
     dist, rank, world = dist_init()
     if args.impl == "reference":
         return run_reference(args, rank, world, dist)

@@ -213,6 +213,88 @@ wfp_status wfp_local_noalloc(int64_t M, const double* src_xy, int64_t Mt, const 
                              const double* sigma_win, int nmax, double dt, double band_limit, double tol,
                              double* u_local, void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Request server: many independent evaluations (each a full problem of Sec. 1 over its own
+ * N_t steps) share one GPU by continuous batching.  The paper evaluates one problem at a time;
+ * the server only schedules plans and adds no arithmetic of its own.
+ *
+ * Each request carries its geometry and its signal parameters; signals are generated on the
+ * device each step, so a request needs no host traffic until its result is read.
+ * wfp_server_tick():
+ *   1. admits pending requests, in arrival order, whose estimated device footprint fits the
+ *      free part of hbm_budget_bytes (a request that does not fit waits; later, smaller ones may
+ *      pass it); a request is admitted with its S history stored (WFP_LAG_STORE) when that
+ *      footprint fits, else with the lagged NUFFT (WFP_LAG_RECOMPUTE); at most max_active
+ *      requests are active at once; a request larger than the whole budget fails;
+ *   2. enqueues one step of every active request, each on its own stream, so that kernels of
+ *      different requests overlap on the device; the host runs at most two steps ahead of the
+ *      device per request (before enqueueing step n it waits for step n - 2);
+ *   3. retires requests that took their last step (it waits for that step, copies the result to
+ *      host memory and frees the request's device memory).
+ * A request's outputs are bitwise the same whether it runs alone or among others.
+ * Not thread-safe: one thread drives a server.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct wfp_server_s* wfp_server;
+
+/* Signal families generated on the device.
+ * WFP_SIGNAL_GAUSS3: 8 doubles per source [a1 a2 a3 c1 c2 c3 s w],
+ *   sigma_j(t) = sum_q a_q exp(-(t - c_q)^2 / (2 s^2)) sin(w (t - c_q)) for t > 0, 0 for t <= 0
+ *   (Gaussian-modulated pulses, the kind of signals of the paper's examples, Sec. 7). */
+enum { WFP_SIGNAL_GAUSS3 = 0 };
+
+typedef struct {
+    int64_t M;                    /* sources (>= 1) */
+    const double* src_xy;         /* host, 2*M doubles; copied by wfp_server_submit */
+    int64_t Mt;                   /* targets (>= 1) */
+    const double* tgt_xy;         /* host, 2*Mt doubles, or NULL for targets = sources (then Mt = M) */
+    double dt;                    /* as wfp_plan_create */
+    int64_t Nt;
+    double band_limit;
+    double tol;
+    int signal_family;            /* WFP_SIGNAL_GAUSS3 */
+    const double* signal_params;  /* host, 8*M doubles; copied */
+    int n_out;                    /* number of output steps; 0 => the final step N_t only */
+    const int64_t* out_steps;     /* host, n_out step indices in 1..N_t (any order; kept sorted) */
+} wfp_request;
+
+enum { WFP_REQ_PENDING = 0, WFP_REQ_ACTIVE = 1, WFP_REQ_DONE = 2, WFP_REQ_FAILED = 3 };
+
+typedef struct {
+    int state;                    /* WFP_REQ_* */
+    int64_t steps_done, Nt, Mt;
+    int n_out;                    /* outputs kept: the result holds n_out * Mt doubles */
+    double t_submit, t_admit, t_done;  /* host steady-clock seconds (same clock for all requests) */
+    int64_t device_bytes;         /* footprint used for admission (estimate) */
+    int64_t plan_bytes;           /* device memory the plan actually held (0 before admission) */
+} wfp_request_status;
+
+/* Create a server.  opts (NULL for defaults) apply to every request, except lag_mode and stream,
+ * which the server chooses.  Errors: WFP_EINVAL, WFP_ENOMEM. */
+wfp_status wfp_server_create(int64_t hbm_budget_bytes, int max_active, const wfp_opts* opts, wfp_server* out);
+
+/* Queue a request; *id receives its id (> 0).  Copies everything it needs from *req.
+ * Errors: WFP_EINVAL (bad sizes, output step outside 1..Nt), WFP_EUNSUPPORTED (signal family). */
+wfp_status wfp_server_submit(wfp_server server, const wfp_request* req, int64_t* id);
+
+/* One round of admission, stepping and retirement (see above).  *n_active and *n_pending
+ * (either may be NULL) receive the counts after the round.  A request whose plan cannot be
+ * built or whose step fails is marked WFP_REQ_FAILED; the server carries on. */
+wfp_status wfp_server_tick(wfp_server server, int* n_active, int* n_pending);
+
+/* Tick until no request is pending or active.  WFP_ENOMEM if pending requests remain that can
+ * not be admitted with nothing active. */
+wfp_status wfp_server_run(wfp_server server);
+
+/* State and timestamps of a request. */
+wfp_status wfp_server_query(wfp_server server, int64_t id, wfp_request_status* status);
+
+/* Copy a finished request's outputs, n_out * Mt doubles (row r = step out_steps[r] in ascending
+ * order), into host memory u_out.  WFP_ESTATE if the request is not done or failed. */
+wfp_status wfp_server_result(wfp_server server, int64_t id, double* u_out);
+
+/* Free every plan and buffer of the server (active requests are abandoned).  NULL is accepted. */
+wfp_status wfp_server_destroy(wfp_server server);
+
 /* Human-readable name of a status code, and the thread-local message of the last failure. */
 const char* wfp_status_string(wfp_status s);
 const char* wfp_last_error(void);

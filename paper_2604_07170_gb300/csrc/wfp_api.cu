@@ -186,7 +186,7 @@ static wfp_status enqueue_step(Plan& pl, bool do_advance, bool lag_now, cudaEven
         ProfScope ps(pl, PP_COPY);
         if (u_dev_dst)
             e = cudaMemcpyAsync(u_dev_dst, pl.d_u_out, pl.Mt * sizeof(double), cudaMemcpyDeviceToDevice, pl.stream);
-        else
+        else if (u_host_stage)
             e = cudaMemcpyAsync(u_host_stage, pl.d_u_out, pl.Mt * sizeof(double), cudaMemcpyDeviceToHost,
                                 pl.stream);
     }
@@ -207,6 +207,32 @@ static wfp_status enqueue_step(Plan& pl, bool do_advance, bool lag_now, cudaEven
         return step_tick(pl, err);
     }, err);
 }
+
+namespace wfp {
+// One step whose input sigma_n is already in pl.d_sig_in (caller order), enqueued on pl.stream; the
+// output is copied to u_dev (device) when non-NULL.  Used by the server's device-side signal source.
+wfp_status plan_step_device(Plan& pl, double* u_dev, std::string& err) {
+    if (pl.poisoned) {
+        err = "plan is poisoned";
+        return WFP_ESTATE;
+    }
+    if (pl.step >= pl.P.Nt) {
+        err = "all Nt steps have been taken";
+        return WFP_ESTATE;
+    }
+    const int64_t n = pl.step + 1;
+    bool adv = n < pl.P.Nt;
+    bool lag_now = pl.P.lag_active && (n - pl.P.L >= 1);
+    wfp_status st = enqueue_step(pl, adv, lag_now, nullptr, u_dev, nullptr, err);
+    if (st != WFP_OK) {
+        pl.poisoned = true;
+        return st;
+    }
+    pl.step = n;
+    return WFP_OK;
+}
+Plan& plan_of(wfp_plan h) { return h->pl; }
+}  // namespace wfp
 
 extern "C" {
 

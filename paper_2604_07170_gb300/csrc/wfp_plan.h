@@ -174,6 +174,8 @@ struct ProfScope {
     ~ProfScope() { stop(); }
 };
 void prof_collect(Plan& pl);  // synchronise and fold recorded pairs into prof_ms / prof_n
+wfp_status plan_step_device(Plan& pl, double* u_dev, std::string& err);  // input already in d_sig_in
+Plan& plan_of(wfp_plan h);
 
 wfp_status plan_build(Plan& pl, const double* src_xy, const double* tgt_xy, std::string& err);
 void plan_free(Plan& pl);

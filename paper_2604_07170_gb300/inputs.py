@@ -185,3 +185,23 @@ def small(M: int, box: float, n_steps: int, seed: int, curve: bool = False, dt: 
     par = gauss3_params(M, T if spread is None else spread, rng, lead=lead)
     return Workload(f"small{M}", xy, par, "gauss3", dt, n_steps, band_limit(par, "gauss3", tol / 1000), tol,
                     {"box": box, "seed": seed})
+
+
+# ---------------------------------------------------------------- serving mix
+def serve_requests(n: int, seed: int = 0, tol: float = 1e-6, dt: float = 0.1) -> list[Workload]:
+    """A mix of independent requests for the request server: M log-uniform in [1e3, 1e5], N_t uniform
+    in [500, 4000], points on max(1, M/1700) random ellipses (semi-axes 1/15..4/15 of the box).  The
+    box side is 0.3 sqrt(M) x U[0.8, 1.25], clipped to [10, 100] wavelengths, which keeps the point
+    density along the curves near that of the 10^4- and 10^5-point ellipse workloads."""
+    rng = np.random.Generator(np.random.PCG64(SEED0 + 104729 * (seed + 1)))
+    eps = tol / 1000.0
+    out = []
+    for i in range(n):
+        M = int(round(math.exp(rng.uniform(math.log(1e3), math.log(1e5)))))
+        Nt = int(rng.integers(500, 4001))
+        box = float(np.clip(0.3 * math.sqrt(M) * rng.uniform(0.8, 1.25), 10.0, 100.0))
+        xy = ellipses(M, max(1, M // 1700), box / 15, 4 * box / 15, box, rng)
+        par = gauss3_params(M, Nt * dt, rng)
+        out.append(Workload(f"req{i}", xy, par, "gauss3", dt, Nt, band_limit(par, "gauss3", eps), tol,
+                            {"box": box, "seed": seed, "index": i}))
+    return out

@@ -51,7 +51,26 @@ _lib = None
 EXPORTS = ["wfp_opts_default", "wfp_plan_create", "wfp_step", "wfp_destroy", "wfp_plan_get_info",
            "wfp_step_components", "wfp_select_params", "wfp_status_string", "wfp_last_error",
            "wfp_profile", "wfp_profile_read", "wfp_local_noalloc", "wfp_debug_eta", "wfp_debug_taps", "wfp_debug_phi",
-           "wfp_debug_soe", "wfp_debug_hankel"]
+           "wfp_debug_soe", "wfp_debug_hankel", "wfp_server_create", "wfp_server_submit", "wfp_server_tick",
+           "wfp_server_run", "wfp_server_query", "wfp_server_result", "wfp_server_destroy"]
+
+SIGNAL_GAUSS3 = 0
+REQ_PENDING, REQ_ACTIVE, REQ_DONE, REQ_FAILED = range(4)
+
+
+class wfp_request(ctypes.Structure):
+    _fields_ = [("M", _c_i64), ("src_xy", _pd), ("Mt", _c_i64), ("tgt_xy", _pd), ("dt", _c_dbl), ("Nt", _c_i64),
+                ("band_limit", _c_dbl), ("tol", _c_dbl), ("signal_family", ctypes.c_int),
+                ("signal_params", _pd), ("n_out", ctypes.c_int), ("out_steps", ctypes.POINTER(_c_i64))]
+
+
+class wfp_request_status(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("steps_done", _c_i64), ("Nt", _c_i64), ("Mt", _c_i64),
+                ("n_out", ctypes.c_int), ("t_submit", _c_dbl), ("t_admit", _c_dbl), ("t_done", _c_dbl),
+                ("device_bytes", _c_i64), ("plan_bytes", _c_i64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def lib():
@@ -86,6 +105,16 @@ def lib():
     L.wfp_debug_soe.argtypes = [_c_dbl, ctypes.c_int, ctypes.c_int, _pd, _pd]
     L.wfp_debug_hankel.argtypes = [_c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_dbl, ctypes.c_int, ctypes.c_int, _pd]
     L.wfp_debug_hankel.restype = ctypes.c_int
+    L.wfp_server_create.argtypes = [_c_i64, ctypes.c_int, ctypes.POINTER(wfp_opts), ctypes.POINTER(vp)]
+    L.wfp_server_submit.argtypes = [vp, ctypes.POINTER(wfp_request), ctypes.POINTER(_c_i64)]
+    L.wfp_server_tick.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.wfp_server_run.argtypes = [vp]
+    L.wfp_server_query.argtypes = [vp, _c_i64, ctypes.POINTER(wfp_request_status)]
+    L.wfp_server_result.argtypes = [vp, _c_i64, _pd]
+    L.wfp_server_destroy.argtypes = [vp]
+    for name in ("wfp_server_create", "wfp_server_submit", "wfp_server_tick", "wfp_server_run",
+                 "wfp_server_query", "wfp_server_result", "wfp_server_destroy"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("wfp_plan_create", "wfp_step", "wfp_destroy", "wfp_plan_get_info", "wfp_step_components",
                  "wfp_profile", "wfp_profile_read",
                  "wfp_select_params", "wfp_debug_eta", "wfp_debug_taps", "wfp_debug_phi", "wfp_debug_soe"):
@@ -212,6 +241,68 @@ def local_noalloc(src_xy, tgt_xy, sigma_win, nmax: int, dt: float, band_limit: f
     _check(lib().wfp_local_noalloc(M, p(src_xy), Mt, p(tgt_xy), p(sigma_win), int(nmax), dt, band_limit, tol,
                                    p(out), ctypes.c_void_p(stream or 0)), "wfp_local_noalloc")
     return out
+
+
+class Server:
+    """Continuous-batching request server (wfp_server_* in include/wfp.h)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 64, **opts):
+        h = ctypes.c_void_p()
+        _check(lib().wfp_server_create(int(hbm_budget_bytes), int(max_active), ctypes.byref(default_opts(**opts)),
+                                       ctypes.byref(h)), "wfp_server_create")
+        self._h = h
+
+    def submit(self, src_xy, signal_params, dt: float, Nt: int, band_limit: float, tol: float = 1e-6,
+               tgt_xy=None, out_steps=None) -> int:
+        src = np.ascontiguousarray(src_xy, dtype=np.float64)
+        par = np.ascontiguousarray(signal_params, dtype=np.float64)
+        assert par.shape == (src.shape[0], 8)
+        tgt = None if tgt_xy is None else np.ascontiguousarray(tgt_xy, dtype=np.float64)
+        steps = None if out_steps is None else np.ascontiguousarray(out_steps, dtype=np.int64)
+        q = wfp_request(M=src.shape[0], src_xy=_dptr(src), Mt=(src if tgt is None else tgt).shape[0],
+                        tgt_xy=None if tgt is None else _dptr(tgt), dt=dt, Nt=int(Nt), band_limit=band_limit,
+                        tol=tol, signal_family=SIGNAL_GAUSS3, signal_params=_dptr(par),
+                        n_out=0 if steps is None else steps.size,
+                        out_steps=None if steps is None else steps.ctypes.data_as(ctypes.POINTER(_c_i64)))
+        rid = _c_i64()
+        _check(lib().wfp_server_submit(self._h, ctypes.byref(q), ctypes.byref(rid)), "wfp_server_submit")
+        return rid.value
+
+    def tick(self):
+        a, p = ctypes.c_int(), ctypes.c_int()
+        _check(lib().wfp_server_tick(self._h, ctypes.byref(a), ctypes.byref(p)), "wfp_server_tick")
+        return a.value, p.value
+
+    def run(self):
+        _check(lib().wfp_server_run(self._h), "wfp_server_run")
+
+    def query(self, rid: int) -> dict:
+        st = wfp_request_status()
+        _check(lib().wfp_server_query(self._h, rid, ctypes.byref(st)), "wfp_server_query")
+        return st.as_dict()
+
+    def result(self, rid: int) -> np.ndarray:
+        st = self.query(rid)
+        out = np.zeros((st["n_out"], st["Mt"]))
+        _check(lib().wfp_server_result(self._h, rid, _dptr(out)), "wfp_server_result")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().wfp_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ host-only diagnostics

@@ -196,3 +196,31 @@ def test_mode_recurrence_matches_direct_quadrature_and_forgets_removed_signal():
         # value is 0 and the recurrence keeps only eps-level residue of the injected-then-removed pulse
         assert abs(checks[520][1]) < 1e-12 * scale
         assert abs(checks[520][0]) < 1e-9 * scale
+
+
+def test_server_rejects_bad_requests_on_the_host():
+    # submission is host-only: validation happens before any device work
+    sv = wfp.Server(1 << 30, 4)
+    xy = np.zeros((3, 2))
+    xy[:, 0] = [0.0, 1.0, 2.0]
+    par = np.zeros((3, 8))
+    with pytest.raises(wfp.WFPError) as ei:
+        sv.submit(xy, par, 0.1, 10, 5.0, 1e-6, out_steps=[0])          # step outside 1..Nt
+    assert ei.value.code == wfp.WFP_EINVAL
+    with pytest.raises(wfp.WFPError) as ei:
+        sv.submit(xy, par, 0.1, 10, 5.0, 1e-6, out_steps=[11])
+    assert ei.value.code == wfp.WFP_EINVAL
+    with pytest.raises(wfp.WFPError) as ei:
+        sv.submit(xy, par, 0.1, 0, 5.0, 1e-6)                          # Nt < 1
+    assert ei.value.code == wfp.WFP_EINVAL
+    rid = sv.submit(xy, par, 0.1, 10, 5.0, 1e-6, out_steps=[10, 3])
+    st = sv.query(rid)
+    assert st["state"] == wfp.REQ_PENDING and st["n_out"] == 2 and st["Mt"] == 3
+    with pytest.raises(wfp.WFPError) as ei:
+        sv.result(rid)
+    assert ei.value.code == wfp.WFP_ESTATE
+    q = wfp.wfp_request(M=3, src_xy=wfp._dptr(np.ascontiguousarray(xy)), Mt=3, dt=0.1, Nt=10, band_limit=5.0,
+                        tol=1e-6, signal_family=7, signal_params=wfp._dptr(par))
+    rid2 = ctypes.c_int64()
+    assert wfp.lib().wfp_server_submit(sv._h, ctypes.byref(q), ctypes.byref(rid2)) == wfp.WFP_EUNSUPPORTED
+    sv.close()
