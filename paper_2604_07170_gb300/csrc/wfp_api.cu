@@ -386,7 +386,7 @@ wfp_status wfp_debug_taps(double kappa, double dt, int W, double eps, double lag
             f1[(size_t)m * ngt + q] = dphi_host(sq[q] + m * dt, delta, b);
             f2[(size_t)m * ngt + q] = d2phi_host(sq[q] + m * dt, delta, b);
         }
-    mode_taps<double>(kappa, dt, W, lagshift, ngt, sq.data(), wq.data(), f1.data(), f2.data(), taps, rot);
+    mode_taps(kappa, dt, W, lagshift, ngt, sq.data(), wq.data(), f1.data(), f2.data(), TapsPlanar{taps, W}, rot);
     return WFP_OK;
 }
 

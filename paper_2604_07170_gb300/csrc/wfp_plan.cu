@@ -100,32 +100,35 @@ __global__ void __launch_bounds__(128) k_eta(int64_t npairs, const double* __res
     if (k >= npairs) return;
     double e[kMaxLevels];
     eta_weights(rr[k], dt, W, p, nmax, phicoef, gx, gw, ng, wl, Cls, e);
-    for (int l = 0; l < NW; l++) eta[k * NW + l] = (l < nmax) ? (TW)e[l] : (TW)0;
+    // with NW = 32 the row is aligned with the linear window (position NW - nmax + l holds level l)
+    const int off = (NW == 32) ? NW - nmax : 0;
+    for (int i = 0; i < NW; i++) eta[k * NW + i] = (i >= off && i - off < nmax) ? (TW)e[i - off] : (TW)0;
 }
 
 // ------------------------------------------------------------------- FIR taps
-// taps [kid][4W] in the reduced precision: p_m, q_m, pA_m, qA_m (Eq. hggrid), dt folded in
+// taps per distinct |k|, interleaved by level m: FP64 {p_m, q_m, pA_m, qA_m} (Eq. hggrid, dt folded
+// in), or FP32 hi parts followed by lo parts ([kid][W][8]) on the mixed path
 template <typename TT>
 __global__ void k_taps(int64_t nk, const double* __restrict__ kap, double dt, int W, double lagshift, int ngt,
                        const double* __restrict__ sq, const double* __restrict__ wq, const double* __restrict__ f1,
                        const double* __restrict__ f2, TT* __restrict__ taps, double* __restrict__ rot) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nk) return;
-    mode_taps<TT>(kap[i], dt, W, lagshift, ngt, sq, wq, f1, f2, taps + i * 4 * W, rot + 3 * i);
+    const int per = (sizeof(TT) == 8) ? 4 : 8;
+    mode_taps(kap[i], dt, W, lagshift, ngt, sq, wq, f1, f2, TapsInterleaved<TT>{taps + i * per * W}, rot + 3 * i);
 }
 
 // v -> (hi, lo) float pair rows of length W, or double rows
-template <typename TT>
-static void put_taps(std::vector<TT>& out, size_t row, int W, const std::vector<double>& v) {
-    if constexpr (sizeof(TT) == 8) {
-        for (int j = 0; j < W; j++) out[row * W + j] = (TT)v[j];
-    } else {
-        for (int j = 0; j < W; j++) {
-            float hi = (float)v[j];
-            out[row * 2 * W + j] = hi;
-            out[row * 2 * W + W + j] = (float)(v[j] - (double)hi);
-        }
-    }
+// head taps of the far recurrence: ffir[k][q] = sum_l H[k][l] coef[l][q]
+__global__ void k_far_head(int nfk, int nlam, int Wh, const double* __restrict__ H, const double* __restrict__ coef,
+                           double* __restrict__ ffir) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)nfk * Wh) return;
+    int64_t k = i / Wh;
+    int qq = (int)(i - k * Wh);
+    double acc = 0.0;
+    for (int l = 0; l < nlam; l++) acc = fma(H[k * nlam + l], coef[(int64_t)l * Wh + qq], acc);
+    ffir[i] = acc;
 }
 
 // ------------------------------------------------------------------- Hankel coefficients (Eq. H)
@@ -374,7 +377,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(upload_tmp(d_f1, f1));
         CK(upload_tmp(d_f2, f2));
         T* taps = nullptr;
-        CK(mem.alloc(&taps, (size_t)pl.n_kappa * 4 * P.W));
+        CK(mem.alloc(&taps, (size_t)pl.n_kappa * (sizeof(T) == 8 ? 4 : 8) * P.W));
         pl.d_taps = taps;
         CK(mem.alloc(&pl.d_rot, (size_t)pl.n_kappa * 3));
         k_taps<T><<<nblk(pl.n_kappa, 128), 128>>>(pl.n_kappa, d_kap.p, P.dt, P.W, P.Aplus - P.delta, ngt, d_sq.p,
@@ -431,22 +434,31 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(mem.alloc(&pl.d_H, (size_t)nfk * P.n_lambda));
         k_hankel<<<nfk, 256, nr * sizeof(double)>>>(nfk, P.n_lambda, nr, d_fkap.p, d_rn.p, d_tab.p, pl.d_H);
         CK(cudaGetLastError());
-        // forcing taps c_{l,m} = dt exp(-lam_l ((L+1+m) dt - A)) [phi((W-m) dt) - phi((W-1-m) dt)]
-        std::vector<T> ftap((size_t)P.n_lambda * P.W * (sizeof(T) == 8 ? 1 : 2));
-        std::vector<double> fdec(P.n_lambda), row(P.W);
+        // The blended far kernel integrated against the trapezoid interpolant of the lagged S gives
+        //   B_l(t_{n+1}) = r_l B_l(t_n) + sum_{m<W} a_l r_l^m d_m S_{n-L-m},
+        //   r_l = exp(-lam_l dt), a_l = dt exp(-lam_l ((L+1) dt - A)), d_m = phi((W-m) dt) - phi((W-1-m) dt).
+        // Unrolled, the partial sums of d_m telescope to P_q = 1 - phi((W-1-q) dt) (= 1 for q >= W-1), so
+        //   alpha_F = sum_l H_l E_l + sum_{q<W-1} Phi_q(|k|) S_{n-L-q},
+        //   E_l(t_{n+1}) = r_l E_l(t_n) + a_l r_l^(W-1) S_{n-L-W+1},
+        //   Phi_q(|k|) = P_q sum_l H_l(|k|) a_l r_l^q
+        // (the split of the far forcing into a one-tap tail recurrence and a FIR over the newest
+        // lagged levels, Sec. 5): the same sums, with one tap per term instead of W.
+        const int Wh = P.W - 1;
+        std::vector<double> fdec(P.n_lambda), ffor(P.n_lambda), coef((size_t)P.n_lambda * std::max(Wh, 1));
         for (int l = 0; l < P.n_lambda; l++) {
             fdec[l] = std::exp(-lam[l] * P.dt);
-            for (int m = 0; m < P.W; m++) {
-                double dphi = phi_host(phic.data(), (P.W - m) * P.dt, P.delta) -
-                              phi_host(phic.data(), (P.W - 1 - m) * P.dt, P.delta);
-                row[m] = P.dt * std::exp(-lam[l] * ((P.L + 1 + m) * P.dt - P.A)) * dphi;
-            }
-            put_taps<T>(ftap, l, P.W, row);
+            ffor[l] = P.dt * std::exp(-lam[l] * ((P.L + P.W) * P.dt - P.A));
+            for (int qq = 0; qq < Wh; qq++)
+                coef[(size_t)l * Wh + qq] = (1.0 - phi_host(phic.data(), (Wh - qq) * P.dt, P.delta)) * P.dt *
+                                            std::exp(-lam[l] * ((P.L + 1 + qq) * P.dt - P.A));
         }
-        T* dft = nullptr;
-        CK(upload(mem, &dft, ftap));
-        pl.d_ftap = dft;
+        Tmp<double> d_coef;
+        CK(upload_tmp(d_coef, coef));
+        CK(mem.alloc(&pl.d_ffir, (size_t)nfk * std::max(Wh, 1)));
+        k_far_head<<<nblk((int64_t)nfk * Wh, 128), 128>>>(nfk, P.n_lambda, Wh, pl.d_H, d_coef.p, pl.d_ffir);
+        CK(cudaGetLastError());
         CK(upload(mem, &pl.d_fdecay, fdec));
+        CK(upload(mem, &pl.d_fforce, ffor));
         CK(mem.alloc(&pl.d_B, (size_t)P.n_lambda * pl.n_far));
         CK(cudaDeviceSynchronize());
     }
@@ -479,26 +491,27 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
             return WFP_EINVAL;
         }
         pl.n_soe_self = (int)lam.size();
-        std::vector<T> stap((size_t)pl.n_soe_self * P.W * (sizeof(T) == 8 ? 1 : 2));
-        std::vector<double> sdec(pl.n_soe_self), sw(pl.n_soe_self), row(P.W);
-        std::vector<int> sntap(pl.n_soe_self);
+        // Y_l(t_{n+1}) = r_l Y_l(t_n) + dt sum_{m<W} r_l^(m+1) [phi((m+1) dt) - phi(m dt)] sigma_{n-m}
+        // (trapezoid on the grid); unrolled, the partial sums telescope to phi((q+1) dt), so
+        //   u_self(t_n) = sum_{q<W-1} g_q sigma_{n-1-q} + sum_l (w_l dt / 2 pi) Z_l(t_n),
+        //   Z_l(t_{n+1}) = r_l Z_l(t_n) + r_l^W sigma_{n+1-W},
+        //   g_q = dt phi((q+1) dt) sum_l (w_l / 2 pi) r_l^(q+1):
+        // one shared W-tap window and a one-tap recurrence per term.
+        const int Wh = P.W - 1;
+        std::vector<double> sdec(pl.n_soe_self), sfor(pl.n_soe_self), sw(pl.n_soe_self), head(std::max(Wh, 1), 0.0);
         for (int l = 0; l < pl.n_soe_self; l++) {
             sdec[l] = std::exp(-lam[l] * P.dt);
-            sw[l] = q[l] / (2.0 * kPi);
-            int nt = 0;
-            for (int m = 0; m < P.W; m++) {
-                double dphi = phi_host(phic.data(), (m + 1) * P.dt, P.delta) - phi_host(phic.data(), m * P.dt, P.delta);
-                row[m] = P.dt * std::exp(-lam[l] * (m + 1) * P.dt) * dphi;
-                if (std::fabs(row[m]) > 1e-30 * P.dt) nt = m + 1;  // later taps are negligible
-            }
-            put_taps<T>(stap, l, P.W, row);
-            sntap[l] = nt;
+            sfor[l] = std::exp(-lam[l] * P.W * P.dt);
+            sw[l] = q[l] / (2.0 * kPi) * P.dt;
         }
-        CK(upload(mem, &pl.d_sntap, sntap));
-        T* dst = nullptr;
-        CK(upload(mem, &dst, stap));
-        pl.d_stap = dst;
+        for (int qq = 0; qq < Wh; qq++) {
+            double acc = 0.0;
+            for (int l = 0; l < pl.n_soe_self; l++) acc += q[l] / (2.0 * kPi) * std::exp(-lam[l] * (qq + 1) * P.dt);
+            head[qq] = P.dt * phi_host(phic.data(), (qq + 1) * P.dt, P.delta) * acc;
+        }
+        CK(upload(mem, &pl.d_shead, head));
         CK(upload(mem, &pl.d_sdecay, sdec));
+        CK(upload(mem, &pl.d_sforce, sfor));
         CK(upload(mem, &pl.d_sw, sw));
         CK(mem.alloc(&pl.d_Y, (size_t)pl.n_soe_self * pl.n_self));
     }
@@ -628,6 +641,10 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         T* w = nullptr;
         CK(mem.alloc(&w, (size_t)M * pl.NW));
         pl.d_sigwin = w;
+        if (pl.NW == 32) {
+            CK(mem.alloc(&w, (size_t)M * 32));
+            pl.d_siglin = w;
+        }
         pl.n_hist = (P.lag_active && !pl.lag_store) ? P.L + 1 : 1;
         CK(mem.alloc(&w, (size_t)pl.n_hist * M));
         pl.d_sighist = w;

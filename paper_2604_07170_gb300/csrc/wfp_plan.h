@@ -56,10 +56,11 @@ struct Plan {
     int64_t n_pairs = 0;
     int64_t* d_rowptr = nullptr;
     int* d_col = nullptr;
-    void* d_eta = nullptr;
+    void* d_eta = nullptr;       // NW = 32: row position 32 - nmax + l holds eta_l (aligned with d_siglin)
 
     // sigma storage
     void* d_sigwin = nullptr;    // [M][NW] window of the last NW levels (slot = level & (NW-1)), reduced precision
+    void* d_siglin = nullptr;    // [M][32] the last 32 levels oldest first (NW = 32 only), reduced precision
     void* d_sighist = nullptr;   // [n_hist][M] in the grid precision (slot = level % n_hist)
     int n_hist = 1;
     double* d_sig_in = nullptr;  // caller-order sigma_n staged on the device
@@ -104,20 +105,21 @@ struct Plan {
     int* d_far_mode = nullptr;   // [n_far] mode index
     int* d_far_k = nullptr;      // [n_far] far-|k| index
     double* d_H = nullptr;       // [n_fkappa][n_lambda] Hankel coefficients (Eq. H)
-    void* d_ftap = nullptr;      // [n_lambda][W] forcing taps of the recurrence (reduced precision)
-    double* d_fdecay = nullptr;  // [n_lambda] exp(-lambda dt)
-    double2* d_B = nullptr;      // [n_lambda][n_far] scaled far coefficients (Eq. beta0)
+    double* d_ffir = nullptr;    // [n_fkappa][W-1] taps of the newest lagged levels, Phi_q(|k|)
+    double* d_fdecay = nullptr;  // [n_lambda] r_l = exp(-lambda_l dt)
+    double* d_fforce = nullptr;  // [n_lambda] a_l r_l^(W-1): weight of S_{n-L-W+1} in the tail recurrence
+    double2* d_B = nullptr;      // [n_lambda][n_far] tail state E_l (scaled by exp(A lambda_l), Eq. beta0)
 
     // self term of coincident pairs
     int64_t n_self = 0;
     int n_soe_self = 0;
     int* d_self_tgt = nullptr;   // internal target
     int* d_self_src = nullptr;   // internal source
-    void* d_stap = nullptr;      // [n_soe_self][W] (reduced precision)
-    double* d_sdecay = nullptr;  // [n_soe_self]
-    double* d_sw = nullptr;      // [n_soe_self] SOE weights / (2 pi)
-    int* d_sntap = nullptr;      // [n_soe_self] number of non-negligible forcing taps
-    double* d_Y = nullptr;       // [n_soe_self][n_self]
+    double* d_shead = nullptr;   // [W-1] shared window weights g_q
+    double* d_sdecay = nullptr;  // [n_soe_self] r_l = exp(-mu_l dt)
+    double* d_sforce = nullptr;  // [n_soe_self] r_l^W
+    double* d_sw = nullptr;      // [n_soe_self] SOE weights * dt / (2 pi)
+    double* d_Y = nullptr;       // [n_soe_self][n_self] tail state Z_l
 
     // outputs (internal target order)
     double* d_uloc = nullptr;

@@ -124,9 +124,46 @@ WFP_HD inline double sin_over(double k, double x) {
 // The trapezoid rule on the step grid for F (Eq. alphakF) gives one tap per level m = 0..W-1.
 // s nodes (sq, wq on [0, dt]) and phi', phi'' at s + m dt (f1, f2: [W][ngt]) are precomputed.
 // rot = {cos(kappa dt), sin(kappa dt)/kappa, kappa sin(kappa dt)}.
+// Tap writers: planar [p | q | pA | qA] (W each, FP64), or interleaved per level m: FP64
+// {p, q, pA, qA}, FP32 {p, q, pA, qA} rounded followed by their rounding residuals (hi/lo pairs).
+struct TapsPlanar {
+    double* t;
+    int W;
+    WFP_HD void operator()(int m, double p, double q, double pa, double qa) const {
+        t[m] = p;
+        t[W + m] = q;
+        t[2 * W + m] = pa;
+        t[3 * W + m] = qa;
+    }
+};
 template <typename TT>
+struct TapsInterleaved;
+template <>
+struct TapsInterleaved<double> {
+    double* t;
+    WFP_HD void operator()(int m, double p, double q, double pa, double qa) const {
+        t[4 * m] = p;
+        t[4 * m + 1] = q;
+        t[4 * m + 2] = pa;
+        t[4 * m + 3] = qa;
+    }
+};
+template <>
+struct TapsInterleaved<float> {
+    float* t;
+    WFP_HD void operator()(int m, double p, double q, double pa, double qa) const {
+        const double v[4] = {p, q, pa, qa};
+        for (int i = 0; i < 4; i++) {
+            float hi = (float)v[i];
+            t[8 * m + i] = hi;
+            t[8 * m + 4 + i] = (float)(v[i] - (double)hi);
+        }
+    }
+};
+
+template <typename Put>
 WFP_HD inline void mode_taps(double kappa, double dt, int W, double lagshift, int ngt, const double* sq,
-                             const double* wq, const double* f1, const double* f2, TT* taps, double* rot) {
+                             const double* wq, const double* f1, const double* f2, const Put& put, double* rot) {
     for (int m = 0; m < W; m++) {
         double P = 0, Q = 0, PA = 0, QA = 0;
         for (int q = 0; q < ngt; q++) {
@@ -142,10 +179,7 @@ WFP_HD inline void mode_taps(double kappa, double dt, int W, double lagshift, in
             PA += wgt * sk * psiA;
             QA += wgt * ck * psiA;
         }
-        taps[m] = (TT)(dt * P);
-        taps[W + m] = (TT)(dt * Q);
-        taps[2 * W + m] = (TT)(dt * PA);
-        taps[3 * W + m] = (TT)(dt * QA);
+        put(m, dt * P, dt * Q, dt * PA, dt * QA);
     }
     rot[0] = cos(kappa * dt);
     rot[1] = sin_over(kappa, dt);

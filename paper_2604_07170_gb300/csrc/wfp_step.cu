@@ -49,24 +49,52 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // ------------------------------------------------------------------------------------ ingest
-// sigma(t_n) in caller order -> FP64/FP32 window [M][NW] (slot n & (NW-1)) and the level-major
-// history [n_hist][M] in the grid precision (slot n % n_hist) read by both spreads.
+// sigma(t_n) in caller order -> the window [M][NW] (slot n & (NW-1)), the linear window [M][32]
+// (shifted by one level, newest last; NW = 32 only) and the level-major history [n_hist][M] in
+// the grid precision (slot n % n_hist) read by both spreads.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<double> {
+    using type = double2;
+};
+template <>
+struct Vec16<float> {
+    using type = float4;
+};
+
 template <typename T>
 __global__ void k_ingest(const int64_t* __restrict__ d_step, int64_t M, const double* __restrict__ sig_in,
-                         const int* __restrict__ perm, T* __restrict__ sigwin, int NW, T* __restrict__ sighist,
-                         int n_hist) {
+                         const int* __restrict__ perm, T* __restrict__ sigwin, int NW, T* __restrict__ siglin,
+                         T* __restrict__ sighist, int n_hist) {
+    using V = typename Vec16<T>::type;
+    constexpr int LP = 32 * sizeof(T) / 16;  // 16-byte vectors per 32-level row
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= M) return;
     int64_t n = *d_step + 1;
     double s = sig_in[perm[k]];
     sigwin[k * NW + (n & (NW - 1))] = (T)s;
     sighist[(n % n_hist) * M + k] = (T)s;
+    if (siglin) {
+        V* row = (V*)(siglin + k * 32);
+        V buf[LP];
+#pragma unroll
+        for (int i = 0; i < LP; i++) buf[i] = row[i];
+        const T* t = (const T*)buf;
+        T out[32];
+#pragma unroll
+        for (int i = 0; i < 31; i++) out[i] = t[i + 1];
+        out[31] = (T)s;
+#pragma unroll
+        for (int i = 0; i < LP; i++) row[i] = ((const V*)out)[i];
+    }
 }
 
 // ------------------------------------------------------------------------------- local part
 // u_l(x_i, t_n) = sum_{j in N_delta(i)} sum_{l=1}^{nmax} eta_l(r_ij) sigma_j(t_{n-nmax+l})  (Sec. 6)
 // One warp per target row; lane = time level, so each pair's weight row and each source's
-// sigma window are read as contiguous 32-element segments.  eta carries the 1/(2 pi).
+// sigma window are read as contiguous 32-element segments.  eta carries the 1/(2 pi).  This form
+// serves windows of 64 levels (nmax > 32); k_local_vec below serves nmax <= 32.
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     float y = x - c;
     float t = s + y;
@@ -133,19 +161,87 @@ __global__ void __launch_bounds__(256) k_local(const int64_t* __restrict__ d_ste
     if (lane == 0) uloc[row] = tot;
 }
 
+// Vectorised local part (NW = 32): eta rows are aligned with the linear window, so a pair is a dot
+// product of two 32-level rows read as 16-byte vectors: LP lanes per pair (8 in FP32, 16 in FP64),
+// 32/LP pairs per warp load, four such groups in flight per iteration.  Weights are streamed
+// (read once); the windows are gathered from L2.
+template <typename T>
+__global__ void __launch_bounds__(256) k_local_vec(int64_t Mt, const int64_t* __restrict__ rowptr,
+                                                   const int* __restrict__ col, const T* __restrict__ eta,
+                                                   const T* __restrict__ siglin, double* __restrict__ uloc) {
+    using V = typename Vec16<T>::type;
+    constexpr int LP = 32 * sizeof(T) / 16;  // lanes per pair
+    constexpr int PW = 32 / LP;              // pairs per warp load
+    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (row >= Mt) return;
+    const int c = lane % LP, g = lane / LP;
+    const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
+    const V* E = (const V*)eta;
+    const V* X = (const V*)siglin;
+    double tot;
+    if constexpr (sizeof(T) == 8) {
+        double a0 = 0.0, a1 = 0.0;
+        int64_t p = p0 + g;
+        for (; p + 3 * PW < p1; p += 4 * PW) {
+            const int j0 = col[p], j1 = col[p + PW], j2 = col[p + 2 * PW], j3 = col[p + 3 * PW];
+            const V e0 = __ldcs(E + p * LP + c), e1 = __ldcs(E + (p + PW) * LP + c);
+            const V e2 = __ldcs(E + (p + 2 * PW) * LP + c), e3 = __ldcs(E + (p + 3 * PW) * LP + c);
+            const V x0 = __ldg(X + (int64_t)j0 * LP + c), x1 = __ldg(X + (int64_t)j1 * LP + c);
+            const V x2 = __ldg(X + (int64_t)j2 * LP + c), x3 = __ldg(X + (int64_t)j3 * LP + c);
+            a0 = fma(e0.x, x0.x, a0);
+            a1 = fma(e0.y, x0.y, a1);
+            a0 = fma(e1.x, x1.x, a0);
+            a1 = fma(e1.y, x1.y, a1);
+            a0 = fma(e2.x, x2.x, a0);
+            a1 = fma(e2.y, x2.y, a1);
+            a0 = fma(e3.x, x3.x, a0);
+            a1 = fma(e3.y, x3.y, a1);
+        }
+        for (; p < p1; p += PW) {
+            const V e = __ldcs(E + p * LP + c), x = __ldg(X + (int64_t)col[p] * LP + c);
+            a0 = fma(e.x, x.x, a0);
+            a1 = fma(e.y, x.y, a1);
+        }
+        tot = a0 + a1;
+    } else {
+        // FP32 products, compensated FP32 accumulation per lane, FP64 across lanes
+        float sm = 0.f, cm = 0.f;
+        int64_t p = p0 + g;
+        for (; p + 3 * PW < p1; p += 4 * PW) {
+            const int j0 = col[p], j1 = col[p + PW], j2 = col[p + 2 * PW], j3 = col[p + 3 * PW];
+            const V e0 = __ldcs(E + p * LP + c), e1 = __ldcs(E + (p + PW) * LP + c);
+            const V e2 = __ldcs(E + (p + 2 * PW) * LP + c), e3 = __ldcs(E + (p + 3 * PW) * LP + c);
+            const V x0 = __ldg(X + (int64_t)j0 * LP + c), x1 = __ldg(X + (int64_t)j1 * LP + c);
+            const V x2 = __ldg(X + (int64_t)j2 * LP + c), x3 = __ldg(X + (int64_t)j3 * LP + c);
+            kahan_add(sm, cm, fmaf(e0.w, x0.w, fmaf(e0.z, x0.z, fmaf(e0.y, x0.y, e0.x * x0.x))));
+            kahan_add(sm, cm, fmaf(e1.w, x1.w, fmaf(e1.z, x1.z, fmaf(e1.y, x1.y, e1.x * x1.x))));
+            kahan_add(sm, cm, fmaf(e2.w, x2.w, fmaf(e2.z, x2.z, fmaf(e2.y, x2.y, e2.x * x2.x))));
+            kahan_add(sm, cm, fmaf(e3.w, x3.w, fmaf(e3.z, x3.z, fmaf(e3.y, x3.y, e3.x * x3.x))));
+        }
+        for (; p < p1; p += PW) {
+            const V e = __ldcs(E + p * LP + c), x = __ldg(X + (int64_t)col[p] * LP + c);
+            kahan_add(sm, cm, fmaf(e.w, x.w, fmaf(e.z, x.z, fmaf(e.y, x.y, e.x * x.x))));
+        }
+        tot = (double)sm - (double)cm;
+    }
+    tot = warp_sum(tot);
+    if (lane == 0) uloc[row] = tot;
+}
+
 // -------------------------------------------------------------------------------- self term
-// u_self,i(t_n) = (1/2pi) int_0^t phi(d) sigma_i(t_n - d)/d dd = sum_l (w_l/2pi) Y_l(t_n), with
-// 1/d ~ sum_l w_l exp(-mu_l d) and Y_l(t) = int exp(-mu_l d) phi(d) sigma(t - d) dd advanced by
-// Y_l(t_{n+1}) = exp(-mu_l dt) Y_l(t_n) + sum_{m<W} e_{l,m} sigma(t_{n-m})  (trapezoid on the grid).
-constexpr int kMaxW = 32;     // W <= 32 (the paper uses 10..30)
+// u_self,i(t_n) = (1/2pi) int_0^t phi(d) sigma_i(t_n - d)/d dd, with 1/d ~ sum_l w_l exp(-mu_l d) on
+// [d_lo, T] and the trapezoid rule on the grid, arranged as a shared window plus one-tap recurrences:
+//   u_self(t_n) = sum_{q<W-1} g_q sigma_{n-1-q} + sum_l w'_l Z_l(t_n),
+//   Z_l(t_{n+1}) = r_l Z_l(t_n) + r_l^W sigma_{n+1-W}.
 constexpr int kMaxWFar = 32;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_self(const int64_t* __restrict__ d_step, int64_t n_self,
                                               const int* __restrict__ self_tgt, const int* __restrict__ self_src,
                                               const T* __restrict__ sigwin, int NW, int W, int nsoe,
-                                              const T* __restrict__ stap, const int* __restrict__ sntap,
-                                              const double* __restrict__ sdecay, const double* __restrict__ sw,
+                                              const double* __restrict__ shead, const double* __restrict__ sdecay,
+                                              const double* __restrict__ sforce, const double* __restrict__ sw,
                                               double* __restrict__ Y, double* __restrict__ uself) {
     // block (32, 8): 32 coincident targets x 8 interleaved groups of SOE terms
     __shared__ double s_red[8][32];
@@ -153,35 +249,25 @@ __global__ void __launch_bounds__(256) k_self(const int64_t* __restrict__ d_step
     int g = threadIdx.y;
     double u = 0.0;
     if (s < n_self) {
-        int64_t n = *d_step + 1;
-        int src = self_src[s];
-        T sig[kMaxW];
-#pragma unroll
-        for (int m = 0; m < kMaxW; m++) sig[m] = (m < W) ? sigwin[(int64_t)src * NW + ((n - m) & (NW - 1))] : (T)0;
-        for (int l = g; l < nsoe; l += 8) {
-            double y = Y[(int64_t)l * n_self + s];
-            u = fma(sw[l], y, u);
-            const int nt = sntap[l];  // terms with large decay rates see only the newest levels
-            double fd;
-            if constexpr (sizeof(T) == 8) {
-                const T* e = stap + (int64_t)l * W;
-                T f0 = 0, f1 = 0;  // two partial sums shorten the dependent FMA chain
-#pragma unroll
-                for (int m = 0; m < kMaxW; m += 2) {
-                    if (m < nt) f0 += e[m] * sig[m];
-                    if (m + 1 < nt) f1 += e[m + 1] * sig[m + 1];
-                }
-                fd = f0 + f1;
-            } else {  // hi/lo taps, double-float sum
-                const float* e = (const float*)stap + (int64_t)l * 2 * W;
-                float fh = 0, fl = 0;
-#pragma unroll
-                for (int m = 0; m < kMaxW; m++)
-                    if (m < nt) df_acc(fh, fl, e[m], e[W + m], (float)sig[m]);
-                fd = (double)fh + (double)fl;
-            }
-            Y[(int64_t)l * n_self + s] = fma(sdecay[l], y, fd);
+        const int64_t n = *d_step + 1;
+        const T* win = sigwin + (int64_t)self_src[s] * NW;
+        for (int q = g; q < W - 1; q += 8) u = fma(shead[q], (double)win[(n - 1 - q) & (NW - 1)], u);
+        const double x = (double)win[(n + 1 - W) & (NW - 1)];
+        double u2 = 0.0;  // second partial sum shortens the dependent chain
+        int l = g;
+        for (; l + 8 < nsoe; l += 16) {
+            double z0 = Y[(int64_t)l * n_self + s], z1 = Y[(int64_t)(l + 8) * n_self + s];
+            u = fma(sw[l], z0, u);
+            u2 = fma(sw[l + 8], z1, u2);
+            Y[(int64_t)l * n_self + s] = fma(sdecay[l], z0, sforce[l] * x);
+            Y[(int64_t)(l + 8) * n_self + s] = fma(sdecay[l + 8], z1, sforce[l + 8] * x);
         }
+        if (l < nsoe) {
+            double z = Y[(int64_t)l * n_self + s];
+            u = fma(sw[l], z, u);
+            Y[(int64_t)l * n_self + s] = fma(sdecay[l], z, sforce[l] * x);
+        }
+        u += u2;
     }
     s_red[g][threadIdx.x] = u;
     __syncthreads();
@@ -298,8 +384,6 @@ __global__ void __launch_bounds__(256) k_modes(
         s.y = (T)(-(double)t.y * f);
         ring_lag[(int64_t)((n - L + lag_off) % R_lag) * n_modes + m] = s;
     }
-    // FIR in the reduced precision (taps [kid][4W]); the mixed path's FIR rounding is below the
-    // FP32 NUFFT error of S itself
     // the near history is truncated at |k| <= K (Eq. uhtraptrunc); modes between K and the far
     // cut-off carry only S (for the far forcing) and the far coefficient added by k_far
     if ((int64_t)nn.x * nn.x + (int64_t)nn.y * nn.y > near_sq) {
@@ -310,29 +394,58 @@ __global__ void __launch_bounds__(256) k_modes(
         if (nn.y == 0 && nn.x > 0) td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
         return;
     }
-    const T* tp = taps + (int64_t)kid * 4 * W;
-    T hx = 0, hy = 0, gx = 0, gy = 0;
     int sl = slot;                                                      // level n - j
     int sll = (int)((((n - L + lag_off) % R_lag) + R_lag) % R_lag);     // level n - L - j
-    for (int j = 0; j < W; j++) {
-        C a = ring[(int64_t)sl * n_modes + m];
-        T p = tp[j], q = tp[W + j];
-        hx += p * a.x;
-        hy += p * a.y;
-        gx += q * a.x;
-        gy += q * a.y;
-        if (lag) {
-            C b = ring_lag[(int64_t)sll * n_modes + m];
-            T pa = tp[2 * W + j], qa = tp[3 * W + j];
-            hx -= pa * b.x;
-            hy -= pa * b.y;
-            gx -= qa * b.x;
-            gy -= qa * b.y;
+    double hxd, hyd, gxd, gyd;
+    if constexpr (sizeof(T) == 8) {
+        const double2* tp = (const double2*)(taps + (int64_t)kid * 4 * W);  // {p, q}, {pA, qA} per level
+        double hx = 0, hy = 0, gx = 0, gy = 0;
+        for (int j = 0; j < W; j++) {
+            const double2 pq = tp[2 * j];
+            const double2 a = ring[(int64_t)sl * n_modes + m];
+            hx = fma(pq.x, a.x, hx);
+            hy = fma(pq.x, a.y, hy);
+            gx = fma(pq.y, a.x, gx);
+            gy = fma(pq.y, a.y, gy);
+            if (lag) {
+                const double2 pqA = tp[2 * j + 1];
+                const double2 b = ring_lag[(int64_t)sll * n_modes + m];
+                hx = fma(-pqA.x, b.x, hx);
+                hy = fma(-pqA.x, b.y, hy);
+                gx = fma(-pqA.y, b.x, gx);
+                gy = fma(-pqA.y, b.y, gy);
+            }
+            sl = (sl == 0) ? R_cur - 1 : sl - 1;
+            sll = (sll == 0) ? R_lag - 1 : sll - 1;
         }
-        sl = (sl == 0) ? R_cur - 1 : sl - 1;
-        sll = (sll == 0) ? R_lag - 1 : sll - 1;
+        hxd = hx, hyd = hy, gxd = gx, gyd = gy;
+    } else {
+        // hi/lo taps and error-free products summed in double-float: the FIR that adds a level and
+        // the one that removes it L steps later round alike, so nothing persists in alpha
+        const float4* tp = (const float4*)(taps + (int64_t)kid * 8 * W);
+        float hxh = 0, hxl = 0, hyh = 0, hyl = 0, gxh = 0, gxl = 0, gyh = 0, gyl = 0;
+        for (int j = 0; j < W; j++) {
+            const float4 hi = tp[2 * j], lo = tp[2 * j + 1];
+            const float2 a = ring[(int64_t)sl * n_modes + m];
+            df_acc(hxh, hxl, hi.x, lo.x, a.x);
+            df_acc(hyh, hyl, hi.x, lo.x, a.y);
+            df_acc(gxh, gxl, hi.y, lo.y, a.x);
+            df_acc(gyh, gyl, hi.y, lo.y, a.y);
+            if (lag) {
+                const float2 b = ring_lag[(int64_t)sll * n_modes + m];
+                df_acc(hxh, hxl, -hi.z, -lo.z, b.x);
+                df_acc(hyh, hyl, -hi.z, -lo.z, b.y);
+                df_acc(gxh, gxl, -hi.w, -lo.w, b.x);
+                df_acc(gyh, gyl, -hi.w, -lo.w, b.y);
+            }
+            sl = (sl == 0) ? R_cur - 1 : sl - 1;
+            sll = (sll == 0) ? R_lag - 1 : sll - 1;
+        }
+        hxd = (double)hxh + (double)hxl;
+        hyd = (double)hyh + (double)hyl;
+        gxd = (double)gxh + (double)gxl;
+        gyd = (double)gyh + (double)gyl;
     }
-    const double hxd = hx, hyd = hy, gxd = gx, gyd = gy;
     double c = rot[3 * kid], sk = rot[3 * kid + 1], ks = rot[3 * kid + 2];
     double2 a = alpha[m], ad = alphad[m];
     double2 an, adn;
@@ -354,20 +467,21 @@ __global__ void __launch_bounds__(256) k_modes(
 }
 
 // ------------------------------------------------------------------------------ far history
-// For each far mode (|k| <= Kf) and SOE term l (Sec. 5):
-//   B_l(t_{n+1}) = exp(-lam_l dt) B_l(t_n) + sum_{m<W} c_{l,m} S_{n-L-m}
-// (trapezoid rule on the grid applied to the blended far kernel, Eq. beta0 with the exp(A lam)
-// scaling carried in B), then alpha_F = sum_l H_l(|k|) B_l (Eq. alphaFApprox) is added to the
-// type-2 coefficient written by k_modes.  Block (32, 8): 32 far modes x 8 groups of terms.
+// For each far mode (|k| <= Kf), Sec. 5 with the blended far kernel integrated against the
+// trapezoid interpolant of the lagged S on the grid (exp(A lam) scaling carried in the state):
+//   E_l(t_{n+1}) = r_l E_l(t_n) + f_l S_{n-L-W+1}                  (tail recurrence, one tap)
+//   alpha_F = sum_l H_l(|k|) E_l + sum_{q<W-1} Phi_q(|k|) S_{n-L-q}   (Eq. alphaFApprox + newest levels)
+// alpha_F is added to the type-2 coefficient written by k_modes.  Block (32, 8): 32 far modes x 8
+// groups of terms; the W newest lagged levels of the block's modes are staged in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(256) k_far(const int64_t* __restrict__ d_step, int64_t n_far, int64_t n_modes, int W,
                                              int L, int Nh, int nf, int nlam, const int* __restrict__ far_mode,
                                              const int* __restrict__ far_k, const int2* __restrict__ mode_n,
                                              const double* __restrict__ fac, double coef2,
                                              const typename Cplx<T>::type* __restrict__ ring_lag, int R_lag,
-                                             int lag_off, const double* __restrict__ H, const T* __restrict__ ftap,
-                                             const double* __restrict__ fdecay, double2* __restrict__ B,
-                                             typename Cplx<T>::type* __restrict__ td) {
+                                             int lag_off, const double* __restrict__ H, const double* __restrict__ ffir,
+                                             const double* __restrict__ fdecay, const double* __restrict__ fforce,
+                                             double2* __restrict__ B, typename Cplx<T>::type* __restrict__ td) {
     using C = typename Cplx<T>::type;
     int64_t n = *d_step + 1;
     if (n - L < 1) return;
@@ -377,7 +491,6 @@ __global__ void __launch_bounds__(256) k_far(const int64_t* __restrict__ d_step,
     int g = threadIdx.y;
     bool valid = f < n_far;
     int64_t m = valid ? far_mode[f] : 0;
-    // stage the W lagged levels S_{n-L-j} of this block's 32 modes
     for (int j = g; j < W; j += 8) {
         int sl = (int)((((n - L - j + lag_off) % R_lag) + R_lag) % R_lag);  // level n - L - j
         C z;
@@ -388,38 +501,23 @@ __global__ void __launch_bounds__(256) k_far(const int64_t* __restrict__ d_step,
     __syncthreads();
     double2 aF = make_double2(0.0, 0.0);
     if (valid) {
-        int fk = far_k[f];
+        const int fk = far_k[f];
+        const double* Fr = ffir + (int64_t)fk * (W - 1);
+        for (int q = g; q < W - 1; q += 8) {
+            C sq = s_S[q][threadIdx.x];
+            aF.x = fma(Fr[q], (double)sq.x, aF.x);
+            aF.y = fma(Fr[q], (double)sq.y, aF.y);
+        }
+        const C st = s_S[W - 1][threadIdx.x];
+        const double sx = st.x, sy = st.y;
         const double* Hr = H + (int64_t)fk * nlam;
         for (int l = g; l < nlam; l += 8) {
-            double fxd, fyd;
-            if constexpr (sizeof(T) == 8) {
-                const T* cl = ftap + (int64_t)l * W;
-                T fx = 0, fy = 0;
-                for (int j = 0; j < W; j++) {
-                    T cj = cl[j];
-                    C sj = s_S[j][threadIdx.x];
-                    fx += cj * sj.x;
-                    fy += cj * sj.y;
-                }
-                fxd = fx;
-                fyd = fy;
-            } else {  // hi/lo taps, double-float sums: slowly decaying terms do not accumulate FP32 rounding
-                const float* cl = (const float*)ftap + (int64_t)l * 2 * W;
-                float xh = 0, xl = 0, yh = 0, yl = 0;
-                for (int j = 0; j < W; j++) {
-                    C sj = s_S[j][threadIdx.x];
-                    df_acc(xh, xl, cl[j], cl[W + j], sj.x);
-                    df_acc(yh, yl, cl[j], cl[W + j], sj.y);
-                }
-                fxd = (double)xh + (double)xl;
-                fyd = (double)yh + (double)yl;
-            }
             double2 b = B[(int64_t)l * n_far + f];
-            double d = fdecay[l];
-            b.x = fma(d, b.x, fxd);
-            b.y = fma(d, b.y, fyd);
+            const double d = fdecay[l], fo = fforce[l];
+            b.x = fma(d, b.x, fo * sx);
+            b.y = fma(d, b.y, fo * sy);
             B[(int64_t)l * n_far + f] = b;
-            double hl = Hr[l];
+            const double hl = Hr[l];
             aF.x = fma(hl, b.x, aF.x);
             aF.y = fma(hl, b.y, aF.y);
         }
@@ -517,20 +615,26 @@ static wfp_status output_t(Plan& pl, std::string& err) {
     cudaStream_t st = pl.stream;
     ProfScope ps0(pl, PP_INGEST);
     k_ingest<T><<<nblk(pl.M, 256), 256, 0, st>>>(pl.d_step, pl.M, pl.d_sig_in, pl.d_src_perm, (T*)pl.d_sigwin,
-                                                   pl.NW, (T*)pl.d_sighist, pl.n_hist);
+                                                   pl.NW, (T*)pl.d_siglin, (T*)pl.d_sighist, pl.n_hist);
     CK(cudaGetLastError());
     ps0.stop();
     if (pl.Mt > 0) {
         ProfScope ps(pl, PP_LOCAL);
-        k_local<T><<<nblk(pl.Mt * 32, 256), 256, 0, st>>>(pl.d_step, pl.Mt, pl.d_rowptr, pl.d_col, (const T*)pl.d_eta,
-                                                          (const T*)pl.d_sigwin, pl.NW, P.nmax, pl.d_uloc);
+        if (pl.NW == 32)
+            k_local_vec<T><<<nblk(pl.Mt * 32, 256), 256, 0, st>>>(pl.Mt, pl.d_rowptr, pl.d_col, (const T*)pl.d_eta,
+                                                                  (const T*)pl.d_siglin, pl.d_uloc);
+        else
+            k_local<T><<<nblk(pl.Mt * 32, 256), 256, 0, st>>>(pl.d_step, pl.Mt, pl.d_rowptr, pl.d_col,
+                                                              (const T*)pl.d_eta, (const T*)pl.d_sigwin, pl.NW, P.nmax,
+                                                              pl.d_uloc);
         CK(cudaGetLastError());
     }
     if (pl.n_self > 0) {
         ProfScope ps(pl, PP_SELF);
         k_self<T><<<nblk(pl.n_self, 32), dim3(32, 8), 0, st>>>(pl.d_step, pl.n_self, pl.d_self_tgt, pl.d_self_src,
-                                                        (const T*)pl.d_sigwin, pl.NW, P.W, pl.n_soe_self,
-                                                        (const T*)pl.d_stap, pl.d_sntap, pl.d_sdecay, pl.d_sw, pl.d_Y, pl.d_uself);
+                                                               (const T*)pl.d_sigwin, pl.NW, P.W, pl.n_soe_self,
+                                                               pl.d_shead, pl.d_sdecay, pl.d_sforce, pl.d_sw, pl.d_Y,
+                                                               pl.d_uself);
         CK(cudaGetLastError());
     }
     {
@@ -626,8 +730,8 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err) {
         dim3 blk(32, 8);
         k_far<T><<<nblk(pl.n_far, 32), blk, 0, st>>>(pl.d_step, pl.n_far, pl.n_modes, P.W, P.L, P.Nh, P.nf,
                                                       P.n_lambda, pl.d_far_mode, pl.d_far_k, pl.d_mode_n, pl.d_fac,
-                                                      coef2, (const C*)pl.d_ring_lag, pl.R_lag, pl.lag_off, pl.d_H, (const T*)pl.d_ftap, pl.d_fdecay,
-                                                      pl.d_B, (C*)pl.d_td);
+                                                      coef2, (const C*)pl.d_ring_lag, pl.R_lag, pl.lag_off, pl.d_H,
+                                                      pl.d_ffir, pl.d_fdecay, pl.d_fforce, pl.d_B, (C*)pl.d_td);
         CK(cudaGetLastError());
     }
     // type-2: columns (C2C, inverse) then band rows (C2R); the C2R input beyond column Nh is re-zeroed
