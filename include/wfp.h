@@ -59,8 +59,10 @@ enum { WFP_FP64 = 0, WFP_MIXED = 1 };
  *   p             interpolation order of the local part (Sec. 6); 0 => 20, lowered (even, >= 8) so
  *                 that nmax = W + 1 + p/2 <= 32.
  *   Kf            far-history cut-off wavenumber in normalised units (Sec. 5); 0 => derived from eps.
- *   upsampfac     NUFFT fine-grid upsampling factor; 0 => 2.0.
- *   kernel_width  NUFFT spreading-kernel width in grid points; 0 => from eps and upsampfac.
+ *   upsampfac     minimum NUFFT fine-grid upsampling factor; 0 => 1.25 (FP64) or 2.0 (MIXED).  The grid
+ *                 size n_f is the smallest 2^a, 3*2^a or 9*2^a at or above upsampfac * (2 Nh + 1).
+ *   kernel_width  NUFFT spreading-kernel width in grid points; 0 => from eps and the effective
+ *                 upsampling n_f / (2 Nh + 1).
  *   soe_nodes     Gauss-Legendre nodes per dyadic panel of the far sum of exponentials
  *                 (Sec. 2.3, Eq. LaplaceApprox); 0 => the smallest of 16..32 meeting eps.
  *   exclude_self  1 (default): for a target coincident with a source (distance <= 1e-12 of the
@@ -72,6 +74,10 @@ enum { WFP_FP64 = 0, WFP_MIXED = 1 };
  *                 the stored signal history, as the paper does (Sec. 4.3); WFP_LAG_STORE keeps the
  *                 last L + W levels of S per mode in device memory; WFP_LAG_AUTO (0, default) stores
  *                 when that history takes at most 40% of the free device memory, else recomputes.
+ *   spread_tile   side of the grid tile one CTA spreads onto (16 or 32); 0 => chosen at plan time by
+ *                 timing both.  spread_chunk: sources staged in shared memory per round (32 or 64);
+ *                 0 => timed likewise.  Every grid point sums its sources in ascending internal order
+ *                 whatever the tiling, so these choices do not change any result bit.
  */
 typedef struct {
     int precision;
@@ -86,6 +92,8 @@ typedef struct {
     void* stream;
     int use_graph;
     int lag_mode;
+    int spread_tile;
+    int spread_chunk;
 } wfp_opts;
 
 enum { WFP_LAG_AUTO = 0, WFP_LAG_RECOMPUTE = 1, WFP_LAG_STORE = 2 };
@@ -116,6 +124,7 @@ typedef struct {
     int64_t device_bytes;            /* device memory held by the plan */
     int lag_store;                   /* 1: S history stored (L + W levels), 0: lagged NUFFT */
     int64_t s_levels;                /* levels of S kept per mode */
+    int spread_tile, spread_chunk;   /* spreading tile side and staging chunk in use */
 } wfp_info;
 
 typedef struct wfp_plan_s* wfp_plan;

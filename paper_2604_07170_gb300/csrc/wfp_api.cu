@@ -291,6 +291,8 @@ wfp_status wfp_plan_get_info(wfp_plan plan, wfp_info* info) {
     info->device_bytes = pl.mem.bytes;
     info->lag_store = pl.lag_store;
     info->s_levels = pl.R_cur;
+    info->spread_tile = pl.spread_ts;
+    info->spread_chunk = pl.spread_ch;
     return WFP_OK;
 }
 

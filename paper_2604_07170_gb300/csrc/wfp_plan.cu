@@ -210,6 +210,37 @@ static void point_kernel(const Params& P, double xs, double ys, int& off, T* ker
 }
 
 // ------------------------------------------------------------------- plan build
+// Non-empty ts x ts tiles of the band and the sources whose footprint touches each, in ascending
+// internal source order (tile coordinates packed tx | ty << 16).
+struct TileLists {
+    std::vector<int> txy, tptr, tsrc;
+    bool made = false;
+};
+
+static TileLists build_tiles(const Params& P, const std::vector<int>& soff, int ts) {
+    TileLists t;
+    const int ntx = P.nb / ts;
+    std::vector<std::pair<int, int>> pairs;
+    pairs.reserve(soff.size() * 3);
+    for (size_t k = 0; k < soff.size(); k++) {
+        int ix0 = soff[k] & 0xffff, iy0 = soff[k] >> 16;
+        for (int ty = iy0 / ts; ty <= (iy0 + P.w - 1) / ts; ty++)
+            for (int tx = ix0 / ts; tx <= (ix0 + P.w - 1) / ts; tx++) pairs.push_back({ty * ntx + tx, (int)k});
+    }
+    std::sort(pairs.begin(), pairs.end());
+    for (size_t i = 0; i < pairs.size(); i++) {
+        if (i == 0 || pairs[i].first != pairs[i - 1].first) {
+            int tt = pairs[i].first;
+            t.txy.push_back((tt % ntx) | ((tt / ntx) << 16));
+            t.tptr.push_back((int)i);
+        }
+        t.tsrc.push_back(pairs[i].second);
+    }
+    t.tptr.push_back((int)pairs.size());
+    t.made = true;
+    return t;
+}
+
 template <typename T>
 static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::vector<double>& txy, std::string& err) {
     using C = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
@@ -318,7 +349,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(cudaDeviceSynchronize());
     }
 
-    // ---- near-history modes: half-plane disk |n| dk <= Km, rows n1 = 0..Nh, -Nh..-1, columns n2 ascending
+    // ---- near-history modes: half-plane disk |n| dk <= Km (n2 > 0, or n2 = 0 and n1 >= 0)
     const int Nh = P.Nh;
     const double R2 = (P.Km / P.dk) * (P.Km / P.dk), Rf2 = (P.Kf / P.dk) * (P.Kf / P.dk);
     const int64_t maxsq = (int64_t)std::floor(R2) + 1;
@@ -345,6 +376,11 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
             pl.n_kappa = nk;
         }
     }
+    // modes sorted by |n|^2: the 32 modes of a warp share a few distinct |k|, so the FIR taps (stored
+    // once per |k|) are read by few transactions; the grid gather/scatter of k_modes is by index
+    std::stable_sort(modes.begin(), modes.end(), [](const int2& a, const int2& b) {
+        return (int64_t)a.x * a.x + (int64_t)a.y * a.y < (int64_t)b.x * b.x + (int64_t)b.y * b.y;
+    });
     pl.n_modes = (int64_t)modes.size();
     std::vector<int> mk(pl.n_modes);
     std::vector<double> kap(pl.n_kappa);
@@ -517,6 +553,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
     }
 
     // ---- NUFFT tables: footprints, kernel values, deconvolution factors, spreading tiles
+    TileLists tile_lists[2];  // tile side 16, 32
     {
         if (P.nb >= 32768) {
             err = "NUFFT band too large for 16-bit footprint offsets";
@@ -540,31 +577,18 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         std::vector<double> fac(P.Nh + 1);
         for (int n = 0; n <= P.Nh; n++) fac[n] = ((n & 1) ? -1.0 : 1.0) * P.h / psihat[n];
         CK(upload(mem, &pl.d_fac, fac));
-        // tiles of the band touched by each source footprint
-        int ntx = P.nb / kTile;
-        std::vector<std::pair<int, int>> ts_pairs;
-        ts_pairs.reserve((size_t)M * 2);
-        for (int64_t k = 0; k < M; k++) {
-            int ix0 = soff[k] & 0xffff, iy0 = soff[k] >> 16;
-            for (int ty = iy0 / kTile; ty <= (iy0 + P.w - 1) / kTile; ty++)
-                for (int tx = ix0 / kTile; tx <= (ix0 + P.w - 1) / kTile; tx++)
-                    ts_pairs.push_back({ty * ntx + tx, (int)k});
+        // tiles of the band touched by each source footprint, for each candidate tile side; the
+        // autotuner below times them and keeps one
+        const int opt_ts = pl.opts.spread_tile, opt_ch = pl.opts.spread_chunk;
+        if ((opt_ts != 0 && opt_ts != 16 && opt_ts != 32) || (opt_ch != 0 && opt_ch != 32 && opt_ch != 64)) {
+            err = "spread_tile must be 0, 16 or 32 and spread_chunk 0, 32 or 64";
+            return WFP_EINVAL;
         }
-        std::sort(ts_pairs.begin(), ts_pairs.end());
-        std::vector<int> txy, tptr, tsrc;
-        for (size_t i = 0; i < ts_pairs.size(); i++) {
-            if (i == 0 || ts_pairs[i].first != ts_pairs[i - 1].first) {
-                int t = ts_pairs[i].first;
-                txy.push_back((t % ntx) | ((t / ntx) << 16));
-                tptr.push_back((int)i);
-            }
-            tsrc.push_back(ts_pairs[i].second);
+        for (int ts : {16, 32}) {
+            if (opt_ts != 0 && ts != opt_ts) continue;
+            tile_lists[ts == 16 ? 0 : 1] = build_tiles(P, soff, ts);
         }
-        tptr.push_back((int)ts_pairs.size());
-        pl.n_tiles = (int)txy.size();
-        CK(upload(mem, &pl.d_tile_xy, txy));
-        CK(upload(mem, &pl.d_tile_ptr, tptr));
-        CK(upload(mem, &pl.d_tile_src, tsrc));
+
     }
 
     // ---- lagged S: stored history (L + W levels per mode) or a lagged type-1 NUFFT (Sec. 4.3)
@@ -669,6 +693,63 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
     CK(cudaMallocHost(&pl.h_u, std::max<int64_t>(Mt, 1) * sizeof(double)));
     CK(cudaEventCreateWithFlags(&pl.ev_out, cudaEventDisableTiming));
     CK(cudaDeviceSynchronize());
+
+    // ---- spreading autotuner: every candidate tiling gives the same bits (ascending source order
+    // per grid point), so the fastest on this device and workload is kept
+    {
+        struct Cand {
+            int ts, ch;
+        };
+        std::vector<Cand> cands;
+        for (int ts : {16, 32})
+            if (tile_lists[ts == 16 ? 0 : 1].made)
+                for (int ch : {32, 64})
+                    if (pl.opts.spread_chunk == 0 || ch == pl.opts.spread_chunk) cands.push_back({ts, ch});
+        size_t best = 0;
+        if (cands.size() > 1) {
+            Tmp<int> txy[2], tptr[2], tsrc[2];
+            for (int i = 0; i < 2; i++)
+                if (tile_lists[i].made) {
+                    CK(upload_tmp(txy[i], tile_lists[i].txy));
+                    CK(upload_tmp(tptr[i], tile_lists[i].tptr));
+                    CK(upload_tmp(tsrc[i], tile_lists[i].tsrc));
+                }
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            float best_ms = 1e30f;
+            for (size_t c = 0; c < cands.size(); c++) {
+                const int i = cands[c].ts == 16 ? 0 : 1;
+                const int nt = (int)tile_lists[i].txy.size();
+                for (int r = 0; r < 7; r++) {
+                    if (r == 2) cudaEventRecord(e0, pl.stream);
+                    spread_launch(pl, cands[c].ts, cands[c].ch, 0, nt, txy[i].p, tptr[i].p, tsrc[i].p, pl.d_sp_cur,
+                                  pl.stream);
+                }
+                cudaEventRecord(e1, pl.stream);
+                CK(cudaEventSynchronize(e1));
+                CK(cudaGetLastError());
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            CK(cudaMemsetAsync(pl.d_sp_cur, 0, (size_t)P.nb * P.nf * sizeof(T), pl.stream));
+            CK(cudaStreamSynchronize(pl.stream));
+        }
+        pl.spread_ts = cands[best].ts;
+        pl.spread_ch = cands[best].ch;
+        const TileLists& tl = tile_lists[pl.spread_ts == 16 ? 0 : 1];
+        pl.n_tiles = (int)tl.txy.size();
+        CK(upload(mem, &pl.d_tile_xy, tl.txy));
+        CK(upload(mem, &pl.d_tile_ptr, tl.tptr));
+        CK(upload(mem, &pl.d_tile_src, tl.tsrc));
+        CK(cudaDeviceSynchronize());
+    }
     return WFP_OK;
 }
 

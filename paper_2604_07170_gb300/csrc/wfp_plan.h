@@ -70,6 +70,8 @@ struct Plan {
     void* d_src_ker = nullptr;   // [M][2w] kernel values (x then y), grid precision
     int* d_tgt_off = nullptr;    // [Mt]
     void* d_tgt_ker = nullptr;   // [Mt][2w]
+    int spread_ts = 32;          // spreading tile side (16 or 32)
+    int spread_ch = 64;          // sources staged per round (32 or 64)
     int n_tiles = 0;             // non-empty spreading tiles
     int* d_tile_xy = nullptr;    // [n_tiles] packed (tx, ty)
     int* d_tile_ptr = nullptr;   // [n_tiles + 1]
@@ -87,7 +89,7 @@ struct Plan {
     cufftHandle fftA = 0, fftB = 0, fftBi = 0, fftAi = 0;
     bool fft_made[4] = {false, false, false, false};
 
-    // near-history modes (Sec. 4): half-plane disk, ordered by (row n1, column n2)
+    // near-history modes (Sec. 4): half-plane disk, ordered by |n|^2
     int64_t n_modes = 0, n_kappa = 0;
     int2* d_mode_n = nullptr;    // (n1, n2)
     int* d_mode_k = nullptr;     // distinct-|k| index
@@ -176,7 +178,10 @@ struct ProfScope {
     ~ProfScope() { stop(); }
 };
 void prof_collect(Plan& pl);  // synchronise and fold recorded pairs into prof_ms / prof_n
-wfp_status plan_step_device(Plan& pl, double* u_dev, std::string& err);  // input already in d_sig_in
+wfp_status plan_step_device(Plan& pl, double* u_dev, std::string& err);
+// one spreading launch with the given tiling (plan-time autotuner and step loop)
+void spread_launch(const Plan& pl, int ts, int ch, int lag, int n_tiles, const int* txy, const int* tptr,
+                   const int* tsrc, void* sp, cudaStream_t st);  // input already in d_sig_in
 Plan& plan_of(wfp_plan h);
 
 wfp_status plan_build(Plan& pl, const double* src_xy, const double* tgt_xy, std::string& err);

@@ -287,60 +287,87 @@ __global__ void k_combine(int64_t Mt, const int* __restrict__ tgt_perm, const do
 __global__ void k_tick(int64_t* d_step) { *d_step += 1; }
 
 // ------------------------------------------------------------------------------- spreading
-// Type-1 spreading onto the fine-grid band, one CTA per non-empty 32x32 tile; every grid point
-// sums its sources in the tile's fixed order (no atomics), so the current and the lagged
-// transforms of the same level are bit-identical.  Warp w owns rows w, w+8, w+16, w+24; lane = column.
-constexpr int kSpreadChunk = 64;
-
-template <typename T>
-__global__ void __launch_bounds__(1024) k_spread(const int64_t* __restrict__ d_step, int lag, int L, int64_t M,
-                                                const T* __restrict__ sighist, int n_hist,
-                                                const int* __restrict__ tile_xy, const int* __restrict__ tile_ptr,
-                                                const int* __restrict__ tile_src, const int* __restrict__ src_off,
-                                                const T* __restrict__ src_ker, int w, T* __restrict__ sp, int nf,
-                                                int lb0) {
+// Type-1 spreading onto the fine-grid band, one CTA of TS x TS threads per non-empty TS x TS tile;
+// thread (r, c) owns grid point (r, c) of the tile and sums the sources of the tile's list, which is
+// in ascending internal source order.  A source contributes to a point only through its footprint,
+// so every point sums the same sources in the same order for any TS or CH: no atomics, results
+// independent of the tiling, and the current and lagged transforms of a level bit-identical.
+// Sources are staged CH at a time in shared memory (strength, footprint origin, kernel values).
+template <typename T, int TS, int CH>
+__global__ void __launch_bounds__(TS * TS) k_spread(const int64_t* __restrict__ d_step, int lag, int L, int64_t M,
+                                                    const T* __restrict__ sighist, int n_hist,
+                                                    const int* __restrict__ tile_xy, const int* __restrict__ tile_ptr,
+                                                    const int* __restrict__ tile_src, const int* __restrict__ src_off,
+                                                    const T* __restrict__ src_ker, int w, T* __restrict__ sp, int nf,
+                                                    int lb0) {
     int64_t n = *d_step + 1;
     int64_t lev = lag ? n - L : n;
     if (lev < 1) return;
     const T* sig = sighist + (lev % n_hist) * M;
-    __shared__ T s_val[kSpreadChunk];
-    __shared__ int s_off[kSpreadChunk];
-    __shared__ T s_ker[kSpreadChunk * 48];
-    int t = blockIdx.x;
-    int txy = tile_xy[t];
-    int tx = txy & 0xffff, ty = txy >> 16;
-    int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;  // 32 warps: warp wp owns tile row wp
-    int colb = tx * kTile + lane;
-    const int rowb = ty * kTile + wp;
+    __shared__ T s_val[CH];
+    __shared__ int s_off[CH];
+    __shared__ T s_ker[CH * 48];
+    const int t = blockIdx.x;
+    const int txy = tile_xy[t];
+    const int tx = txy & 0xffff, ty = txy >> 16;
+    const int colb = tx * TS + (int)(threadIdx.x % TS);
+    const int rowb = ty * TS + (int)(threadIdx.x / TS);
     T acc = 0;
-    int a0 = tile_ptr[t], a1 = tile_ptr[t + 1];
-    for (int c0 = a0; c0 < a1; c0 += kSpreadChunk) {
-        int cn = min(kSpreadChunk, a1 - c0);
+    const int a0 = tile_ptr[t], a1 = tile_ptr[t + 1];
+    for (int c0 = a0; c0 < a1; c0 += CH) {
+        const int cn = min(CH, a1 - c0);
         __syncthreads();
-        for (int i = threadIdx.x; i < cn; i += blockDim.x) {
-            int s = tile_src[c0 + i];
-            s_val[i] = sig[s];
-            s_off[i] = src_off[s];
+        for (int i = threadIdx.x; i < cn; i += TS * TS) {
+            int sidx = tile_src[c0 + i];
+            s_val[i] = sig[sidx];
+            s_off[i] = src_off[sidx];
         }
         __syncthreads();
         // x-kernel values are stored pre-multiplied by the source strength
-        for (int i = threadIdx.x; i < cn * 2 * w; i += blockDim.x) {
+        for (int i = threadIdx.x; i < cn * 2 * w; i += TS * TS) {
             int si = i / (2 * w), e = i - si * 2 * w;
             T v = src_ker[(int64_t)tile_src[c0 + si] * 2 * w + e];
             s_ker[si * 48 + e] = (e < w) ? s_val[si] * v : v;
         }
         __syncthreads();
         for (int i = 0; i < cn; i++) {
-            int off = s_off[i];
-            int dy = rowb - (off >> 16);
-            if ((unsigned)dy < (unsigned)w) {  // warp-uniform: this warp's row is in the footprint
-                int dx = colb - (off & 0xffff);
-                T skx = ((unsigned)dx < (unsigned)w) ? s_ker[i * 48 + dx] : (T)0;
-                acc += skx * s_ker[i * 48 + w + dy];
+            const int off = s_off[i];
+            const int dy = rowb - (off >> 16);
+            if ((unsigned)dy < (unsigned)w) {
+                const int dx = colb - (off & 0xffff);
+                const T skx = ((unsigned)dx < (unsigned)w) ? s_ker[i * 48 + dx] : (T)0;
+                acc = fma(skx, s_ker[i * 48 + w + dy], acc);
             }
         }
     }
     sp[(int64_t)rowb * nf + lb0 + colb] = acc;
+}
+
+template <typename T, int TS, int CH>
+static void spread_one(const Plan& pl, int lag, int n_tiles, const int* txy, const int* tptr, const int* tsrc, T* sp,
+                       cudaStream_t st) {
+    const Params& P = pl.P;
+    k_spread<T, TS, CH><<<n_tiles, TS * TS, 0, st>>>(pl.d_step, lag, P.L, pl.M, (const T*)pl.d_sighist, pl.n_hist,
+                                                       txy, tptr, tsrc, pl.d_src_off, (const T*)pl.d_src_ker, P.w, sp,
+                                                       P.nf, P.lb0);
+}
+
+template <typename T>
+static void spread_t(const Plan& pl, int ts, int ch, int lag, int n_tiles, const int* txy, const int* tptr,
+                     const int* tsrc, T* sp, cudaStream_t st) {
+    if (ts == 16)
+        (ch == 32 ? spread_one<T, 16, 32> : spread_one<T, 16, 64>)(pl, lag, n_tiles, txy, tptr, tsrc, sp, st);
+    else
+        (ch == 32 ? spread_one<T, 32, 32> : spread_one<T, 32, 64>)(pl, lag, n_tiles, txy, tptr, tsrc, sp, st);
+}
+
+void spread_launch(const Plan& pl, int ts, int ch, int lag, int n_tiles, const int* txy, const int* tptr,
+                   const int* tsrc, void* sp, cudaStream_t st) {
+    if (n_tiles <= 0) return;
+    if (pl.P.precision == WFP_FP64)
+        spread_t<double>(pl, ts, ch, lag, n_tiles, txy, tptr, tsrc, (double*)sp, st);
+    else
+        spread_t<float>(pl, ts, ch, lag, n_tiles, txy, tptr, tsrc, (float*)sp, st);
 }
 
 // ------------------------------------------------------------------------------ mode update
@@ -687,14 +714,12 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err) {
     // type-1 spreading: current level and (when active) the lagged level
     if (pl.n_tiles > 0) {
         ProfScope ps(pl, PP_SPREAD);
-        k_spread<T><<<pl.n_tiles, 1024, 0, st>>>(pl.d_step, 0, P.L, pl.M, (const T*)pl.d_sighist, pl.n_hist,
-                                                pl.d_tile_xy, pl.d_tile_ptr, pl.d_tile_src, pl.d_src_off,
-                                                (const T*)pl.d_src_ker, P.w, (T*)pl.d_sp_cur, P.nf, P.lb0);
+        spread_t<T>(pl, pl.spread_ts, pl.spread_ch, 0, pl.n_tiles, pl.d_tile_xy, pl.d_tile_ptr, pl.d_tile_src,
+                    (T*)pl.d_sp_cur, st);
         CK(cudaGetLastError());
         if (lag_now && !pl.lag_store) {
-            k_spread<T><<<pl.n_tiles, 1024, 0, st>>>(pl.d_step, 1, P.L, pl.M, (const T*)pl.d_sighist, pl.n_hist,
-                                                    pl.d_tile_xy, pl.d_tile_ptr, pl.d_tile_src, pl.d_src_off,
-                                                    (const T*)pl.d_src_ker, P.w, (T*)pl.d_sp_lag, P.nf, P.lb0);
+            spread_t<T>(pl, pl.spread_ts, pl.spread_ch, 1, pl.n_tiles, pl.d_tile_xy, pl.d_tile_ptr, pl.d_tile_src,
+                        (T*)pl.d_sp_lag, st);
             CK(cudaGetLastError());
         }
     }

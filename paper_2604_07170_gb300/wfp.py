@@ -26,7 +26,8 @@ class wfp_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("eps", _c_dbl), ("W", ctypes.c_int), ("p", ctypes.c_int),
                 ("Kf", _c_dbl), ("upsampfac", _c_dbl), ("kernel_width", ctypes.c_int),
                 ("soe_nodes", ctypes.c_int), ("exclude_self", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("use_graph", ctypes.c_int), ("lag_mode", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("lag_mode", ctypes.c_int), ("spread_tile", ctypes.c_int),
+                ("spread_chunk", ctypes.c_int)]
 
 
 class wfp_info(ctypes.Structure):
@@ -39,7 +40,8 @@ class wfp_info(ctypes.Structure):
                 ("nf", ctypes.c_int), ("nb", ctypes.c_int), ("kernel_width", ctypes.c_int),
                 ("upsampfac", _c_dbl), ("n_pairs", _c_i64), ("n_self", _c_i64), ("lag_active", ctypes.c_int),
                 ("far_active", ctypes.c_int), ("precision", ctypes.c_int), ("device_bytes", _c_i64),
-                ("lag_store", ctypes.c_int), ("s_levels", _c_i64)]
+                ("lag_store", ctypes.c_int), ("s_levels", _c_i64), ("spread_tile", ctypes.c_int),
+                ("spread_chunk", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -157,3 +157,18 @@ def test_cfg2_full_size_mixed_sampled():
     # mixed path: FP32 NUFFT / FFT rounding (~1e-7 of the strengths' sum) persists in the history, so
     # in the tail (field ~1e-2 of its peak and falling) the error relative to the floor grows
     _full_size_parity("cfg2", 1, [400, 800, 1060, 1400], 16, 2e-6, tail=5e-4)
+
+
+def test_spreading_tilings_give_identical_fields():
+    # every grid point sums its sources in ascending order whatever the tile side or staging chunk,
+    # so the autotuner's choice cannot change a bit of the result
+    wl = inputs.small(300, 4.0, 120, seed=19, curve=True)
+    outs = []
+    for ts, ch in ((16, 32), (16, 64), (32, 32), (32, 64)):
+        o, info = _run(wl, 120, spread_tile=ts, spread_chunk=ch)
+        assert info["spread_tile"] == ts and info["spread_chunk"] == ch
+        outs.append(o)
+    auto, info = _run(wl, 120)
+    assert info["spread_tile"] in (16, 32) and info["spread_chunk"] in (32, 64)
+    for o in outs[1:] + [auto]:
+        assert np.array_equal(outs[0], o)
