@@ -78,6 +78,9 @@ enum { WFP_FP64 = 0, WFP_MIXED = 1 };
  *                 timing both.  spread_chunk: sources staged in shared memory per round (32 or 64);
  *                 0 => timed likewise.  Every grid point sums its sources in ascending internal order
  *                 whatever the tiling, so these choices do not change any result bit.
+ *   local_variant kernel of the local part when nmax <= 32: 1 = warp-vector loads, 2..5 = weight rows
+ *                 staged into shared memory by bulk asynchronous copies (four stage/CTA shapes);
+ *                 0 => the fastest, timed at plan time.  All variants give the same bits.
  */
 typedef struct {
     int precision;
@@ -94,6 +97,7 @@ typedef struct {
     int lag_mode;
     int spread_tile;
     int spread_chunk;
+    int local_variant;
 } wfp_opts;
 
 enum { WFP_LAG_AUTO = 0, WFP_LAG_RECOMPUTE = 1, WFP_LAG_STORE = 2 };
@@ -125,6 +129,7 @@ typedef struct {
     int lag_store;                   /* 1: S history stored (L + W levels), 0: lagged NUFFT */
     int64_t s_levels;                /* levels of S kept per mode */
     int spread_tile, spread_chunk;   /* spreading tile side and staging chunk in use */
+    int local_variant;               /* local-part kernel variant in use (0: 64-level window form) */
 } wfp_info;
 
 typedef struct wfp_plan_s* wfp_plan;

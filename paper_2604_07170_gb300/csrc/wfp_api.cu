@@ -139,6 +139,14 @@ static wfp_status poison(Plan& pl, const std::string& msg) {
     return fail(WFP_ECUDA, msg);
 }
 
+// a kernel whose bounded wait ran out has set the host-mapped flag: the step's output is not valid
+static bool device_timed_out(const Plan& pl) { return pl.h_err && *(volatile int*)pl.h_err != 0; }
+
+static wfp_status poison_timeout(Plan& pl) {
+    pl.poisoned = true;
+    return fail(WFP_ETIMEOUT, "a bounded device-side wait ran out (bulk copy not completed)");
+}
+
 // Run one phase of a step on the plan's stream: directly, or replayed from a CUDA graph that is
 // captured on the phase's second use (the first use initialises cuFFT outside any capture).
 template <typename F>
@@ -220,6 +228,11 @@ wfp_status plan_step_device(Plan& pl, double* u_dev, std::string& err) {
         err = "all Nt steps have been taken";
         return WFP_ESTATE;
     }
+    if (device_timed_out(pl)) {
+        pl.poisoned = true;
+        err = "a bounded device-side wait ran out (bulk copy not completed)";
+        return WFP_ETIMEOUT;
+    }
     const int64_t n = pl.step + 1;
     bool adv = n < pl.P.Nt;
     bool lag_now = pl.P.lag_active && (n - pl.P.L >= 1);
@@ -242,6 +255,7 @@ wfp_status wfp_step(wfp_plan plan, const double* sigma_n, double* u_n) {
     if (pl.poisoned) return fail(WFP_ESTATE, "plan is poisoned by an earlier CUDA error");
     if (!sigma_n || !u_n) return fail(WFP_EINVAL, "sigma_n and u_n must not be NULL");
     if (pl.step >= pl.P.Nt) return fail(WFP_ESTATE, "all Nt steps have been taken");
+    if (device_timed_out(pl)) return poison_timeout(pl);
     const int64_t n = pl.step + 1;
     const bool dev_in = is_device_ptr(sigma_n), dev_out = is_device_ptr(u_n);
     cudaError_t e;
@@ -264,6 +278,7 @@ wfp_status wfp_step(wfp_plan plan, const double* sigma_n, double* u_n) {
     if (!dev_out) {
         e = cudaEventSynchronize(pl.ev_out);
         if (e != cudaSuccess) return poison(pl, std::string("step: ") + cudaGetErrorString(e));
+        if (device_timed_out(pl)) return poison_timeout(pl);
         std::memcpy(u_n, pl.h_u, pl.Mt * sizeof(double));
     }
     pl.step = n;
@@ -293,6 +308,7 @@ wfp_status wfp_plan_get_info(wfp_plan plan, wfp_info* info) {
     info->s_levels = pl.R_cur;
     info->spread_tile = pl.spread_ts;
     info->spread_chunk = pl.spread_ch;
+    info->local_variant = pl.NW == 32 ? pl.local_variant : 0;
     return WFP_OK;
 }
 

@@ -293,9 +293,15 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(cudaMemcpy(cnt.data(), d_cnt.p, Mt * sizeof(int), cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(selfj.data(), d_self.p, Mt * sizeof(int), cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(ns.data(), d_ns.p, Mt * sizeof(int), cudaMemcpyDeviceToHost));
+        // rows padded to a multiple of 4 pair slots (zero-weight slots with r = 0, source 0), so that
+        // every row starts 16-byte aligned in the index array for the bulk copies of the local part
         std::vector<int64_t> rowptr(Mt + 1, 0);
-        for (int64_t i = 0; i < Mt; i++) rowptr[i + 1] = rowptr[i] + cnt[i];
-        pl.n_pairs = rowptr[Mt];
+        pl.n_pairs = 0;
+        for (int64_t i = 0; i < Mt; i++) {
+            rowptr[i + 1] = rowptr[i] + ((cnt[i] + 3) & ~3);
+            pl.n_pairs += cnt[i];
+        }
+        pl.n_slots = rowptr[Mt];
         std::vector<int> st, ssrc;
         for (int64_t i = 0; i < Mt; i++) {
             if (ns[i] > 1) {
@@ -315,13 +321,14 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(upload(mem, &pl.d_rowptr, rowptr));
         size_t freeb = 0, totb = 0;
         CK(cudaMemGetInfo(&freeb, &totb));
-        size_t need = (size_t)pl.n_pairs * (sizeof(int) + sizeof(double) + pl.NW * sizeof(T));
+        size_t need = (size_t)pl.n_slots * (sizeof(int) + sizeof(double) + pl.NW * sizeof(T));
         if (need + (size_t)(1ull << 30) > freeb) {
             err = "local weights need " + std::to_string(need >> 20) + " MiB of device memory";
             return WFP_ENOMEM;
         }
-        CK(mem.alloc(&pl.d_col, pl.n_pairs));
-        CK(d_r.alloc(pl.n_pairs));
+        CK(mem.alloc(&pl.d_col, pl.n_slots));
+        CK(d_r.alloc(pl.n_slots));
+        CK(cudaMemset(d_r.p, 0, std::max<size_t>(pl.n_slots, 1) * sizeof(double)));
         k_nbr<<<nblk(Mt, 128), 128>>>(1, Mt, (const double2*)d_t.p, (const double2*)d_s.p, d_cs.p, nc, cs, P.delta,
                                       rc, nullptr, nullptr, nullptr, pl.d_rowptr, pl.d_col, d_r.p);
         CK(cudaGetLastError());
@@ -339,10 +346,10 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(upload_tmp(d_wl, wl));
         CK(upload_tmp(d_bls, bls));
         T* eta = nullptr;
-        CK(mem.alloc(&eta, (size_t)pl.n_pairs * pl.NW));
+        CK(mem.alloc(&eta, (size_t)pl.n_slots * pl.NW));
         pl.d_eta = eta;
-        if (pl.n_pairs > 0) {
-            k_eta<T><<<nblk(pl.n_pairs, 128), 128>>>(pl.n_pairs, d_r.p, P.dt, P.W, P.p, P.nmax, pl.NW, pl.d_phicoef,
+        if (pl.n_slots > 0) {
+            k_eta<T><<<nblk(pl.n_slots, 128), 128>>>(pl.n_slots, d_r.p, P.dt, P.W, P.p, P.nmax, pl.NW, pl.d_phicoef,
                                                      d_gx.p, d_gw.p, ng, d_wl.p, d_bls.p, eta);
             CK(cudaGetLastError());
         }
@@ -689,6 +696,11 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(mem.alloc(&pl.d_uself, Mt));
         CK(mem.alloc(&pl.d_u_out, Mt));
     }
+    CK(cudaHostAlloc(&pl.h_err, sizeof(int), cudaHostAllocMapped));
+    *(volatile int*)pl.h_err = 0;
+    CK(cudaHostGetDevicePointer((void**)&pl.d_err, pl.h_err, 0));
+    local_bulk_setup();
+    CK(cudaGetLastError());
     CK(cudaMallocHost(&pl.h_sig, std::max<int64_t>(M, 1) * sizeof(double)));
     CK(cudaMallocHost(&pl.h_u, std::max<int64_t>(Mt, 1) * sizeof(double)));
     CK(cudaEventCreateWithFlags(&pl.ev_out, cudaEventDisableTiming));
@@ -750,6 +762,44 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(upload(mem, &pl.d_tile_src, tl.tsrc));
         CK(cudaDeviceSynchronize());
     }
+
+    // ---- local-part autotuner: all variants give the same bits; keep the fastest
+    if (pl.NW == 32 && Mt > 0) {
+        const int ov = pl.opts.local_variant;
+        if (ov < 0 || ov > kLocalVariants) {
+            err = "local_variant must be 0 (auto) or 1.." + std::to_string(kLocalVariants);
+            return WFP_EINVAL;
+        }
+        if (ov > 0) {
+            pl.local_variant = ov;
+        } else {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            float best_ms = 1e30f;
+            for (int v = 1; v <= kLocalVariants; v++) {
+                for (int r = 0; r < 6; r++) {
+                    if (r == 2) cudaEventRecord(e0, pl.stream);
+                    local_launch(pl, v, pl.stream);
+                }
+                cudaEventRecord(e1, pl.stream);
+                CK(cudaEventSynchronize(e1));
+                CK(cudaGetLastError());
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    pl.local_variant = v;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (*(volatile int*)pl.h_err) {
+                err = "a bounded device-side wait ran out while timing the local part";
+                return WFP_ETIMEOUT;
+            }
+        }
+    }
     return WFP_OK;
 }
 
@@ -806,6 +856,7 @@ void plan_free(Plan& pl) {
     pl.mem.release();
     if (pl.h_sig) cudaFreeHost(pl.h_sig);
     if (pl.h_u) cudaFreeHost(pl.h_u);
+    if (pl.h_err) cudaFreeHost(pl.h_err);
     if (pl.ev_out) cudaEventDestroy(pl.ev_out);
     if (pl.own_stream && pl.stream) cudaStreamDestroy(pl.stream);
 }

@@ -53,7 +53,8 @@ struct Plan {
     int NW = 32;                 // sigma window length (power of two >= nmax)
 
     // local part (Sec. 6): CSR by internal target, weights [pair][NW]
-    int64_t n_pairs = 0;
+    int64_t n_pairs = 0;         // source-target pairs with 0 < r < delta
+    int64_t n_slots = 0;         // pair slots: each row padded to a multiple of 4 (zero weights)
     int64_t* d_rowptr = nullptr;
     int* d_col = nullptr;
     void* d_eta = nullptr;       // NW = 32: row position 32 - nmax + l holds eta_l (aligned with d_siglin)
@@ -70,6 +71,7 @@ struct Plan {
     void* d_src_ker = nullptr;   // [M][2w] kernel values (x then y), grid precision
     int* d_tgt_off = nullptr;    // [Mt]
     void* d_tgt_ker = nullptr;   // [Mt][2w]
+    int local_variant = 1;       // local-part kernel variant (NW = 32), all bit-identical
     int spread_ts = 32;          // spreading tile side (16 or 32)
     int spread_ch = 64;          // sources staged per round (32 or 64)
     int n_tiles = 0;             // non-empty spreading tiles
@@ -129,6 +131,10 @@ struct Plan {
     double* d_uself = nullptr;
     double* d_u_out = nullptr;   // caller order
 
+    // device-side error flag (a bounded wait that ran out), host-mapped pinned memory
+    int* h_err = nullptr;
+    int* d_err = nullptr;
+
     // host staging
     double* h_sig = nullptr;     // pinned
     double* h_u = nullptr;       // pinned
@@ -179,6 +185,9 @@ struct ProfScope {
 };
 void prof_collect(Plan& pl);  // synchronise and fold recorded pairs into prof_ms / prof_n
 wfp_status plan_step_device(Plan& pl, double* u_dev, std::string& err);
+void local_bulk_setup();  // raises the dynamic shared-memory limit of the staged local kernels
+constexpr int kLocalVariants = 5;  // 1 = warp-vector loads, 2..5 = bulk-staged configurations
+void local_launch(const Plan& pl, int variant, cudaStream_t st);
 // one spreading launch with the given tiling (plan-time autotuner and step loop)
 void spread_launch(const Plan& pl, int ts, int ch, int lag, int n_tiles, const int* txy, const int* tptr,
                    const int* tsrc, void* sp, cudaStream_t st);  // input already in d_sig_in

@@ -27,7 +27,7 @@ class wfp_opts(ctypes.Structure):
                 ("Kf", _c_dbl), ("upsampfac", _c_dbl), ("kernel_width", ctypes.c_int),
                 ("soe_nodes", ctypes.c_int), ("exclude_self", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("use_graph", ctypes.c_int), ("lag_mode", ctypes.c_int), ("spread_tile", ctypes.c_int),
-                ("spread_chunk", ctypes.c_int)]
+                ("spread_chunk", ctypes.c_int), ("local_variant", ctypes.c_int)]
 
 
 class wfp_info(ctypes.Structure):
@@ -41,7 +41,7 @@ class wfp_info(ctypes.Structure):
                 ("upsampfac", _c_dbl), ("n_pairs", _c_i64), ("n_self", _c_i64), ("lag_active", ctypes.c_int),
                 ("far_active", ctypes.c_int), ("precision", ctypes.c_int), ("device_bytes", _c_i64),
                 ("lag_store", ctypes.c_int), ("s_levels", _c_i64), ("spread_tile", ctypes.c_int),
-                ("spread_chunk", ctypes.c_int)]
+                ("spread_chunk", ctypes.c_int), ("local_variant", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -172,3 +172,19 @@ def test_spreading_tilings_give_identical_fields():
     assert info["spread_tile"] in (16, 32) and info["spread_chunk"] in (32, 64)
     for o in outs[1:] + [auto]:
         assert np.array_equal(outs[0], o)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_local_variants_give_identical_fields(precision):
+    # the warp-vector kernel and every bulk-staged configuration sum each lane's pairs in the same
+    # order with the same arithmetic, so the autotuner's pick cannot change a bit
+    wl = inputs.small(400, 5.0, 90, seed=20, curve=True)
+    outs = []
+    for v in range(1, 6):
+        o, info = _run(wl, 90, precision=precision, local_variant=v)
+        assert info["local_variant"] == v
+        outs.append(o)
+    auto, info = _run(wl, 90, precision=precision)
+    assert 1 <= info["local_variant"] <= 5
+    for o in outs[1:] + [auto]:
+        assert np.array_equal(outs[0], o)
