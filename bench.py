@@ -149,15 +149,19 @@ def part_model(info: dict, M: int, Mt: int, fp64: bool) -> dict:
     nb, nfg, w = info["nb"], info["nf"], info["kernel_width"]
     nself, nsoe = info["n_self"], info["n_self_soe"]
     lag = 1  # timed window is in the lagged regime
+    spreads = 1 + (lag and not info["lag_store"])  # a second (lagged) spread only without the stored S history
+    tapw = 4 * W * s if fp64 else 8 * W * 4     # FIR taps per |k|: FP64, or FP32 hi/lo pairs
     m = {}
     m["local"] = (npair * (NW * s + 4) + M * NW * s + Mt * (8 + 8), 2 * npair * info["nmax"])
-    m["self"] = (nself * (nsoe * 16 + W * s + 12), nself * nsoe * (2 * W + 4))
-    m["ingest"] = (M * (8 + 4 + 2 * s), 0)
+    # shared window (W levels) + one-tap recurrences: Z_l read and written, FP64
+    m["self"] = (nself * (nsoe * 16 + W * s + 12), nself * (nsoe * 4 + 2 * W))
+    m["ingest"] = (M * (8 + 4 + 2 * s + (2 * NW * s if NW == 32 else 0)), 0)
     m["combine"] = (Mt * (4 + 4 * 8), Mt * 2)
-    m["spread"] = ((1 + lag) * (nb * nb * s + M * (2 * w * s + 4 + s)), (1 + lag) * 2 * M * w * w)
-    m["modes"] = (nm * ((1 + lag) * (W * c + c) + 4 * 16 + 12 + (1 + lag) * c + c) + nk * 4 * W * s,
-                  nm * (8 * W * (1 + lag) + 16))
-    m["far"] = (nf_ * (nl * 32 + W * c + 16) + nl * W * s, nf_ * nl * (4 * W + 8))
+    m["spread"] = (spreads * (nb * nb * s + M * (2 * w * s + 4 + s)), spreads * 2 * M * w * w)
+    # S read and ring write, W ring levels (current and lagged), alpha/alphadot read+write, grid write
+    m["modes"] = (nm * ((1 + lag) * W * c + 2 * c + 4 * 16 + 12 + c) + nk * tapw, nm * (8 * W * (1 + lag) + 16))
+    # E_l read+write (FP64 complex) and H_l per term, W lagged levels, grid read+write
+    m["far"] = (nf_ * (nl * (32 + 8) + W * c + 2 * c), nf_ * (nl * 8 + 4 * W))
     m["interp"] = (nb * nb * s + Mt * (2 * w * s + 4 + 8), 2 * Mt * w * w)
     return {k: {"bytes": int(b), "flops": int(f)} for k, (b, f) in m.items()}
 
@@ -307,8 +311,10 @@ def roofline(r: dict, M: int, Mt: int, fp64: bool) -> tuple[dict, dict]:
             with open(tj) as f:
                 tr = json.load(f)
             key = f"{dom}:{'fp64' if fp64 else 'mixed'}"
-            if key in tr and tr[key].get("source_hash") == source_hash():
-                traffic = tr[key]["bytes_per_launch"]
+            ent = tr.get(key, {})
+            variant_ok = dom != "local" or ent.get("local_variant") == r["info"].get("local_variant")
+            if ent.get("source_hash") == source_hash(dom) and variant_ok:
+                traffic = ent["bytes_per_launch"]
         if e["bound"] == "hbm":
             roof = {"kernel": dom, "bound": "hbm", "achieved": round(e["GB/s"], 1), "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": round(e["GB/s"] / peaks["hbm_gbs"], 4), "traffic": traffic,
@@ -321,21 +327,23 @@ def roofline(r: dict, M: int, Mt: int, fp64: bool) -> tuple[dict, dict]:
     return roof, per
 
 
-def source_hash() -> str:
+def source_hash(kernel: str = "local") -> str:
+    """Hash of the sources a kernel is built from (its counters go stale when they change)."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2604_07170_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
-        if fn.endswith((".cu", ".h", ".cpp")):
-            with open(os.path.join(d, fn), "rb") as f:
-                h.update(f.read())
+    files = {"local": ("wfp_local.cu", "wfp_ptx.h", "wfp_dev.h")}.get(kernel, ("wfp_step.cu", "wfp_dev.h"))
+    for fn in files:
+        with open(os.path.join(d, fn), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def launches_per_step(info: dict, n_self: int) -> int:
     """Kernels of this library per step in the lagged regime (cuFFT's own kernels not counted):
-    ingest, local, [self], combine, spread x2 (current, lagged), modes, [far], interp, tick."""
-    return 1 + 1 + (1 if n_self > 0 else 0) + 1 + 2 + 1 + (1 if info["far_active"] else 0) + 1 + 1
+    ingest, local, [self], combine, spread (x2 when the lag is recomputed), modes, [far], interp, tick."""
+    spreads = 1 if info["lag_store"] else 2
+    return 1 + 1 + (1 if n_self > 0 else 0) + 1 + spreads + 1 + (1 if info["far_active"] else 0) + 1 + 1
 
 
 def drive(args):
@@ -465,7 +473,9 @@ def main():
                    "W": info["W"], "p": info["p"], "L": info["L"], "N_modes_half": info["n_modes"],
                    "nf": info["nf"], "n_pairs": info["n_pairs"], "n_lambda": info["n_lambda"],
                    "plan_seconds": round(r["plan_s"], 3), "device_bytes": info["device_bytes"],
-                   "upsampfac": info["upsampfac"], "kernel_width": info["kernel_width"],
+                   "upsampfac": round(info["upsampfac"], 4), "kernel_width": info["kernel_width"],
+                   "lag_store": info["lag_store"], "local_variant": info["local_variant"],
+                   "spread_tile": info["spread_tile"], "spread_chunk": info["spread_chunk"],
                    "plan_opts": args.plan_opts},
         "clocks": r["clocks"],
         "gpu_launches": K * launches_per_step(info, info["n_self"]),

@@ -119,7 +119,7 @@ __global__ void k_taps(int64_t nk, const double* __restrict__ kap, double dt, in
 }
 
 // v -> (hi, lo) float pair rows of length W, or double rows
-// head taps of the far recurrence: ffir[k][q] = sum_l H[k][l] coef[l][q]
+// head taps of the far recurrence: ffir[q][k] = sum_l H[l][k] coef[l][q]
 __global__ void k_far_head(int nfk, int nlam, int Wh, const double* __restrict__ H, const double* __restrict__ coef,
                            double* __restrict__ ffir) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,8 +127,8 @@ __global__ void k_far_head(int nfk, int nlam, int Wh, const double* __restrict__
     int64_t k = i / Wh;
     int qq = (int)(i - k * Wh);
     double acc = 0.0;
-    for (int l = 0; l < nlam; l++) acc = fma(H[k * nlam + l], coef[(int64_t)l * Wh + qq], acc);
-    ffir[i] = acc;
+    for (int l = 0; l < nlam; l++) acc = fma(H[(int64_t)l * nfk + k], coef[(int64_t)l * Wh + qq], acc);
+    ffir[(int64_t)qq * nfk + k] = acc;
 }
 
 // ------------------------------------------------------------------- Hankel coefficients (Eq. H)
@@ -159,7 +159,7 @@ __global__ void k_hankel(int nfk, int nlam, int nr, const double* __restrict__ k
         const double* tl = tab + (int64_t)l * nr;
         double s = 0.0;
         for (int i = 0; i < nr; i++) s = fma(s_j0[i], tl[i], s);
-        H[(int64_t)fk * nlam + l] = s;
+        H[(int64_t)l * nfk + fk] = s;  // [l][fk]: far modes of a warp read neighbouring |k|
     }
 }
 

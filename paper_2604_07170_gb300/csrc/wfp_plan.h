@@ -188,6 +188,7 @@ wfp_status plan_step_device(Plan& pl, double* u_dev, std::string& err);
 void local_bulk_setup();  // raises the dynamic shared-memory limit of the staged local kernels
 constexpr int kLocalVariants = 5;  // 1 = warp-vector loads, 2..5 = bulk-staged configurations
 void local_launch(const Plan& pl, int variant, cudaStream_t st);
+void local_run(const Plan& pl, cudaStream_t st);  // the plan's local-part kernel
 // one spreading launch with the given tiling (plan-time autotuner and step loop)
 void spread_launch(const Plan& pl, int ts, int ch, int lag, int n_tiles, const int* txy, const int* tptr,
                    const int* tsrc, void* sp, cudaStream_t st);  // input already in d_sig_in

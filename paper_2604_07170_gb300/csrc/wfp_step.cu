@@ -14,56 +14,15 @@
 
 #include <cmath>
 
+#include "wfp_dev.h"
 #include "wfp_plan.h"
-#include "wfp_ptx.h"
 
 namespace wfp {
-
-template <typename T>
-struct Cplx;
-template <>
-struct Cplx<double> {
-    using type = double2;
-};
-template <>
-struct Cplx<float> {
-    using type = float2;
-};
-
-// Double-float accumulation (FP32 arithmetic, ~2x24-bit significand): (sh, sl) += (ah + al) * b,
-// with the product ah*b made exact by an FMA and the sum by TwoSum.  Explicit round-to-nearest
-// intrinsics keep the compiler from contracting the error terms away.
-__device__ __forceinline__ void df_acc(float& sh, float& sl, float ah, float al, float b) {
-    float p = __fmul_rn(ah, b);
-    float e = fmaf(ah, b, -p);
-    e = fmaf(al, b, e);
-    float s = __fadd_rn(sh, p);
-    float bb = __fsub_rn(s, sh);
-    float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    sl = __fadd_rn(sl, __fadd_rn(t, e));
-    sh = s;
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // ------------------------------------------------------------------------------------ ingest
 // sigma(t_n) in caller order -> the window [M][NW] (slot n & (NW-1)), the linear window [M][32]
 // (shifted by one level, newest last; NW = 32 only) and the level-major history [n_hist][M] in
 // the grid precision (slot n % n_hist) read by both spreads.
-template <typename T>
-struct Vec16;
-template <>
-struct Vec16<double> {
-    using type = double2;
-};
-template <>
-struct Vec16<float> {
-    using type = float4;
-};
-
 template <typename T>
 __global__ void k_ingest(const int64_t* __restrict__ d_step, int64_t M, const double* __restrict__ sig_in,
                          const int* __restrict__ perm, T* __restrict__ sigwin, int NW, T* __restrict__ siglin,
@@ -91,296 +50,6 @@ __global__ void k_ingest(const int64_t* __restrict__ d_step, int64_t M, const do
     }
 }
 
-// ------------------------------------------------------------------------------- local part
-// u_l(x_i, t_n) = sum_{j in N_delta(i)} sum_{l=1}^{nmax} eta_l(r_ij) sigma_j(t_{n-nmax+l})  (Sec. 6)
-// One warp per target row; lane = time level, so each pair's weight row and each source's
-// sigma window are read as contiguous 32-element segments.  eta carries the 1/(2 pi).  This form
-// serves windows of 64 levels (nmax > 32); k_local_vec below serves nmax <= 32.
-__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
-    float y = x - c;
-    float t = s + y;
-    c = (t - s) - y;
-    s = t;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_local(const int64_t* __restrict__ d_step, int64_t Mt,
-                                               const int64_t* __restrict__ rowptr, const int* __restrict__ col,
-                                               const T* __restrict__ eta, const T* __restrict__ sigwin, int NW,
-                                               int nmax, double* __restrict__ uloc) {
-    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (row >= Mt) return;
-    int64_t n = *d_step + 1;
-    int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
-    int s0 = (int)((n - nmax + 1 + lane) & (NW - 1));
-    int s1 = (int)((n - nmax + 1 + lane + 32) & (NW - 1));
-    double tot;
-    if constexpr (sizeof(T) == 8) {
-        double acc = 0.0;
-        int64_t p = p0;
-        for (; p + 1 < p1; p += 2) {
-            int j0 = col[p], j1 = col[p + 1];
-            double e0 = eta[p * NW + lane], e1 = eta[(p + 1) * NW + lane];
-            double x0 = sigwin[(int64_t)j0 * NW + s0], x1 = sigwin[(int64_t)j1 * NW + s0];
-            acc = fma(e0, x0, acc);
-            acc = fma(e1, x1, acc);
-            if (NW == 64) {
-                acc = fma(eta[p * NW + lane + 32], sigwin[(int64_t)j0 * NW + s1], acc);
-                acc = fma(eta[(p + 1) * NW + lane + 32], sigwin[(int64_t)j1 * NW + s1], acc);
-            }
-        }
-        if (p < p1) {
-            int j0 = col[p];
-            acc = fma(eta[p * NW + lane], sigwin[(int64_t)j0 * NW + s0], acc);
-            if (NW == 64) acc = fma(eta[p * NW + lane + 32], sigwin[(int64_t)j0 * NW + s1], acc);
-        }
-        tot = acc;
-    } else {
-        // FP32 products, compensated FP32 accumulation per lane, FP64 across lanes
-        float s = 0.f, c = 0.f;
-        int64_t p = p0;
-        for (; p + 1 < p1; p += 2) {
-            int j0 = col[p], j1 = col[p + 1];
-            float e0 = eta[p * NW + lane], e1 = eta[(p + 1) * NW + lane];
-            float x0 = sigwin[(int64_t)j0 * NW + s0], x1 = sigwin[(int64_t)j1 * NW + s0];
-            kahan_add(s, c, e0 * x0);
-            kahan_add(s, c, e1 * x1);
-            if (NW == 64) {
-                kahan_add(s, c, eta[p * NW + lane + 32] * sigwin[(int64_t)j0 * NW + s1]);
-                kahan_add(s, c, eta[(p + 1) * NW + lane + 32] * sigwin[(int64_t)j1 * NW + s1]);
-            }
-        }
-        if (p < p1) {
-            int j0 = col[p];
-            kahan_add(s, c, eta[p * NW + lane] * sigwin[(int64_t)j0 * NW + s0]);
-            if (NW == 64) kahan_add(s, c, eta[p * NW + lane + 32] * sigwin[(int64_t)j0 * NW + s1]);
-        }
-        tot = (double)s - (double)c;
-    }
-    tot = warp_sum(tot);
-    if (lane == 0) uloc[row] = tot;
-}
-
-// Vectorised local part (NW = 32): eta rows are aligned with the linear window, so a pair is a dot
-// product of two 32-level rows read as 16-byte vectors: LP lanes per pair (8 in FP32, 16 in FP64),
-// 32/LP pairs per warp load, four such groups in flight per iteration.  Weights are streamed
-// (read once); the windows are gathered from L2.
-template <typename T>
-__global__ void __launch_bounds__(256) k_local_vec(int64_t Mt, const int64_t* __restrict__ rowptr,
-                                                   const int* __restrict__ col, const T* __restrict__ eta,
-                                                   const T* __restrict__ siglin, double* __restrict__ uloc) {
-    using V = typename Vec16<T>::type;
-    constexpr int LP = 32 * sizeof(T) / 16;  // lanes per pair
-    constexpr int PW = 32 / LP;              // pairs per warp load
-    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (row >= Mt) return;
-    const int c = lane % LP, g = lane / LP;
-    const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
-    const V* E = (const V*)eta;
-    const V* X = (const V*)siglin;
-    double tot;
-    if constexpr (sizeof(T) == 8) {
-        double a0 = 0.0, a1 = 0.0;
-        int64_t p = p0 + g;
-        for (; p + 3 * PW < p1; p += 4 * PW) {
-            const int j0 = col[p], j1 = col[p + PW], j2 = col[p + 2 * PW], j3 = col[p + 3 * PW];
-            const V e0 = __ldcs(E + p * LP + c), e1 = __ldcs(E + (p + PW) * LP + c);
-            const V e2 = __ldcs(E + (p + 2 * PW) * LP + c), e3 = __ldcs(E + (p + 3 * PW) * LP + c);
-            const V x0 = __ldg(X + (int64_t)j0 * LP + c), x1 = __ldg(X + (int64_t)j1 * LP + c);
-            const V x2 = __ldg(X + (int64_t)j2 * LP + c), x3 = __ldg(X + (int64_t)j3 * LP + c);
-            a0 = fma(e0.x, x0.x, a0);
-            a1 = fma(e0.y, x0.y, a1);
-            a0 = fma(e1.x, x1.x, a0);
-            a1 = fma(e1.y, x1.y, a1);
-            a0 = fma(e2.x, x2.x, a0);
-            a1 = fma(e2.y, x2.y, a1);
-            a0 = fma(e3.x, x3.x, a0);
-            a1 = fma(e3.y, x3.y, a1);
-        }
-        for (; p < p1; p += PW) {
-            const V e = __ldcs(E + p * LP + c), x = __ldg(X + (int64_t)col[p] * LP + c);
-            a0 = fma(e.x, x.x, a0);
-            a1 = fma(e.y, x.y, a1);
-        }
-        tot = a0 + a1;
-    } else {
-        // FP32 products, compensated FP32 accumulation per lane, FP64 across lanes
-        float sm = 0.f, cm = 0.f;
-        int64_t p = p0 + g;
-        for (; p + 3 * PW < p1; p += 4 * PW) {
-            const int j0 = col[p], j1 = col[p + PW], j2 = col[p + 2 * PW], j3 = col[p + 3 * PW];
-            const V e0 = __ldcs(E + p * LP + c), e1 = __ldcs(E + (p + PW) * LP + c);
-            const V e2 = __ldcs(E + (p + 2 * PW) * LP + c), e3 = __ldcs(E + (p + 3 * PW) * LP + c);
-            const V x0 = __ldg(X + (int64_t)j0 * LP + c), x1 = __ldg(X + (int64_t)j1 * LP + c);
-            const V x2 = __ldg(X + (int64_t)j2 * LP + c), x3 = __ldg(X + (int64_t)j3 * LP + c);
-            kahan_add(sm, cm, fmaf(e0.w, x0.w, fmaf(e0.z, x0.z, fmaf(e0.y, x0.y, e0.x * x0.x))));
-            kahan_add(sm, cm, fmaf(e1.w, x1.w, fmaf(e1.z, x1.z, fmaf(e1.y, x1.y, e1.x * x1.x))));
-            kahan_add(sm, cm, fmaf(e2.w, x2.w, fmaf(e2.z, x2.z, fmaf(e2.y, x2.y, e2.x * x2.x))));
-            kahan_add(sm, cm, fmaf(e3.w, x3.w, fmaf(e3.z, x3.z, fmaf(e3.y, x3.y, e3.x * x3.x))));
-        }
-        for (; p < p1; p += PW) {
-            const V e = __ldcs(E + p * LP + c), x = __ldg(X + (int64_t)col[p] * LP + c);
-            kahan_add(sm, cm, fmaf(e.w, x.w, fmaf(e.z, x.z, fmaf(e.y, x.y, e.x * x.x))));
-        }
-        tot = (double)sm - (double)cm;
-    }
-    tot = warp_sum(tot);
-    if (lane == 0) uloc[row] = tot;
-}
-
-// Local part with the weight stream staged by bulk asynchronous copies (the form used on sm_103a
-// for nmax <= 32).  Each warp owns one target row: lane 0 keeps S stages of CH pair slots (their
-// weight rows and source indices, contiguous in HBM) in flight into a per-warp shared-memory ring,
-// each stage completed on its own mbarrier; the lanes consume a stage as in k_local_vec (weights
-// from shared memory, windows gathered from L2) and lane 0 refills the buffer with the stage S
-// ahead.  Rows are padded to multiples of 4 slots, so every copy is 16-byte aligned and sized.
-// A wait that runs out sets *err (host-mapped) and the warp drains its copies and returns.
-constexpr uint64_t kBulkWaitNs = 2000000000ull;  // 2 s
-
-template <typename T, int CH, int S, int WARPS_>
-struct LocalBulk {
-    static constexpr uint32_t ROWB = 32 * sizeof(T);          // bytes of one weight row
-    static constexpr uint32_t STAGE = CH * ROWB + CH * 4;     // weights + indices
-    static constexpr uint32_t WARPB = S * STAGE + S * 8;      // stages + mbarriers
-    static constexpr int WARPS = WARPS_;
-    static constexpr uint32_t SMEM = WARPS * WARPB;
-};
-
-// Every variant (k_local_vec and each staged configuration) gives lane (c, g) the pairs g, g + PW,
-// g + 2 PW, ... of its row in that order with the same per-pair arithmetic, so all produce the same
-// bits and the plan-time autotuner may pick any of them.
-template <typename T, int CH, int S, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_local_bulk(int64_t Mt, const int64_t* __restrict__ rowptr,
-                                                    const int* __restrict__ col, const T* __restrict__ eta,
-                                                    const T* __restrict__ siglin, double* __restrict__ uloc,
-                                                    int* err) {
-    using V = typename Vec16<T>::type;
-    using G = LocalBulk<T, CH, S, WARPS>;
-    constexpr int LP = 32 * sizeof(T) / 16;  // lanes per pair
-    constexpr int PW = 32 / LP;              // pairs per warp load
-    static_assert(CH % 4 == 0 && CH % PW == 0, "stage must hold whole 4-slot groups");
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t row = (int64_t)blockIdx.x * G::WARPS + warp;
-    if (row >= Mt) return;
-    unsigned char* base = smem + warp * G::WARPB;
-    uint64_t* bar = (uint64_t*)(base + S * G::STAGE);
-    const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
-    const int nst = (int)((p1 - p0 + CH - 1) / CH);
-    if (lane == 0) {
-        for (int s = 0; s < S; s++) mbar_init(bar + s, 1);
-        fence_mbar_init();
-    }
-    __syncwarp();
-    auto issue = [&](int k) {  // stage k of the row into buffer k % S (lane 0)
-        const int b = k % S;
-        const int64_t q0 = p0 + (int64_t)k * CH;
-        const uint32_t np = (uint32_t)min((int64_t)CH, p1 - q0);
-        unsigned char* dst = base + b * G::STAGE;
-        mbar_expect_tx(bar + b, np * G::ROWB + np * 4);
-        bulk_g2s(dst, eta + q0 * 32, np * G::ROWB, bar + b);
-        bulk_g2s(dst + CH * G::ROWB, col + q0, np * 4, bar + b);
-    };
-    if (lane == 0)
-        for (int k = 0; k < min(S, nst); k++) issue(k);
-    const int c = lane % LP, g = lane / LP;
-    const V* X = (const V*)siglin;
-    double d0 = 0.0, d1 = 0.0;  // FP64 path (as k_local_vec)
-    float sm = 0.f, cm = 0.f;                       // FP32 path: compensated sum
-    int k = 0;
-    for (; k < nst; k++) {
-        const int b = k % S;
-        const bool ok = mbar_wait_bounded(bar + b, (uint32_t)((k / S) & 1), kBulkWaitNs);
-        if (!__all_sync(0xffffffffu, ok)) break;
-        const int np = (int)min((int64_t)CH, p1 - p0 - (int64_t)k * CH);
-        const V* E = (const V*)(base + b * G::STAGE);
-        const int* C = (const int*)(base + b * G::STAGE + CH * G::ROWB);
-#pragma unroll 4
-        for (int q = g; q < np; q += PW) {
-            const V e = E[q * LP + c];
-            const V x = __ldg(X + (int64_t)C[q] * LP + c);
-            if constexpr (sizeof(T) == 8) {
-                d0 = fma(e.x, x.x, d0);
-                d1 = fma(e.y, x.y, d1);
-            } else {
-                kahan_add(sm, cm, fmaf(e.w, x.w, fmaf(e.z, x.z, fmaf(e.y, x.y, e.x * x.x))));
-            }
-        }
-        __syncwarp();
-        if (lane == 0 && k + S < nst) {
-            fence_proxy_async_smem();
-            issue(k + S);
-        }
-    }
-    if (k < nst) {  // a wait ran out: record it, let the copies in flight land, leave the row unset
-        if (lane == 0) *(volatile int*)err = 1;
-        for (int j = k; j < min(nst, k + S); j++) mbar_wait_bounded(bar + j % S, (uint32_t)((j / S) & 1), kBulkWaitNs);
-        __syncwarp();
-        return;
-    }
-    double tot;
-    if constexpr (sizeof(T) == 8)
-        tot = d0 + d1;
-    else
-        tot = (double)sm - (double)cm;
-    tot = warp_sum(tot);
-    if (lane == 0) uloc[row] = tot;
-}
-
-static inline unsigned nblk_u(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
-
-// Local-part variants: 1 = k_local_vec; 2.. = staged configurations (CH slots per stage, S stages,
-// WARPS warps per CTA), chosen per precision so that a stage is 2-4 KB of weights.
-template <typename T, int CH, int S, int WARPS>
-static void bulk_one(const Plan& pl, cudaStream_t st) {
-    using G = LocalBulk<T, CH, S, WARPS>;
-    k_local_bulk<T, CH, S, WARPS><<<(unsigned)((pl.Mt + WARPS - 1) / WARPS), WARPS * 32, G::SMEM, st>>>(
-        pl.Mt, pl.d_rowptr, pl.d_col, (const T*)pl.d_eta, (const T*)pl.d_siglin, pl.d_uloc, pl.d_err);
-}
-template <typename T, int CH, int S, int WARPS>
-static void bulk_attr() {
-    cudaFuncSetAttribute(k_local_bulk<T, CH, S, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         LocalBulk<T, CH, S, WARPS>::SMEM);
-}
-
-template <typename T>
-static void local_variant_t(const Plan& pl, int v, cudaStream_t st) {
-    constexpr bool D = sizeof(T) == 8;
-    switch (v) {
-        case 1:
-            k_local_vec<T><<<nblk_u(pl.Mt * 32, 256), 256, 0, st>>>(pl.Mt, pl.d_rowptr, pl.d_col, (const T*)pl.d_eta,
-                                                                    (const T*)pl.d_siglin, pl.d_uloc);
-            break;
-        case 2: bulk_one<T, D ? 16 : 32, 4, 4>(pl, st); break;
-        case 3: bulk_one<T, D ? 8 : 16, 4, 8>(pl, st); break;
-        case 4: bulk_one<T, D ? 8 : 16, 8, 4>(pl, st); break;
-        default: bulk_one<T, D ? 8 : 16, 2, 16>(pl, st); break;
-    }
-}
-
-template <typename T>
-static void local_attrs_t() {
-    constexpr bool D = sizeof(T) == 8;
-    bulk_attr<T, D ? 16 : 32, 4, 4>();
-    bulk_attr<T, D ? 8 : 16, 4, 8>();
-    bulk_attr<T, D ? 8 : 16, 8, 4>();
-    bulk_attr<T, D ? 8 : 16, 2, 16>();
-}
-
-void local_bulk_setup() {
-    local_attrs_t<double>();
-    local_attrs_t<float>();
-}
-
-void local_launch(const Plan& pl, int variant, cudaStream_t st) {
-    if (pl.P.precision == WFP_FP64)
-        local_variant_t<double>(pl, variant, st);
-    else
-        local_variant_t<float>(pl, variant, st);
-}
-
 // -------------------------------------------------------------------------------- self term
 // u_self,i(t_n) = (1/2pi) int_0^t phi(d) sigma_i(t_n - d)/d dd, with 1/d ~ sum_l w_l exp(-mu_l d) on
 // [d_lo, T] and the trapezoid rule on the grid, arranged as a shared window plus one-tap recurrences:
@@ -388,43 +57,39 @@ void local_launch(const Plan& pl, int variant, cudaStream_t st) {
 //   Z_l(t_{n+1}) = r_l Z_l(t_n) + r_l^W sigma_{n+1-W}.
 constexpr int kMaxWFar = 32;
 
+constexpr int kSelfGroups = 16;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_self(const int64_t* __restrict__ d_step, int64_t n_self,
-                                              const int* __restrict__ self_tgt, const int* __restrict__ self_src,
-                                              const T* __restrict__ sigwin, int NW, int W, int nsoe,
-                                              const double* __restrict__ shead, const double* __restrict__ sdecay,
-                                              const double* __restrict__ sforce, const double* __restrict__ sw,
-                                              double* __restrict__ Y, double* __restrict__ uself) {
-    // block (32, 8): 32 coincident targets x 8 interleaved groups of SOE terms
-    __shared__ double s_red[8][32];
+__global__ void __launch_bounds__(32 * kSelfGroups) k_self(const int64_t* __restrict__ d_step, int64_t n_self,
+                                                           const int* __restrict__ self_tgt,
+                                                           const int* __restrict__ self_src,
+                                                           const T* __restrict__ sigwin, int NW, int W, int nsoe,
+                                                           const double* __restrict__ shead,
+                                                           const double* __restrict__ sdecay,
+                                                           const double* __restrict__ sforce,
+                                                           const double* __restrict__ sw, double* __restrict__ Y,
+                                                           double* __restrict__ uself) {
+    // block (32, G): 32 coincident targets x G interleaved groups of SOE terms
+    constexpr int G = kSelfGroups;
+    __shared__ double s_red[G][32];
     int64_t s = (int64_t)blockIdx.x * 32 + threadIdx.x;
     int g = threadIdx.y;
     double u = 0.0;
     if (s < n_self) {
         const int64_t n = *d_step + 1;
         const T* win = sigwin + (int64_t)self_src[s] * NW;
-        for (int q = g; q < W - 1; q += 8) u = fma(shead[q], (double)win[(n - 1 - q) & (NW - 1)], u);
+        for (int q = g; q < W - 1; q += G) u = fma(shead[q], (double)win[(n - 1 - q) & (NW - 1)], u);
         const double x = (double)win[(n + 1 - W) & (NW - 1)];
-        double u2 = 0.0;  // second partial sum shortens the dependent chain
-        int l = g;
-        for (; l + 8 < nsoe; l += 16) {
-            double z0 = Y[(int64_t)l * n_self + s], z1 = Y[(int64_t)(l + 8) * n_self + s];
-            u = fma(sw[l], z0, u);
-            u2 = fma(sw[l + 8], z1, u2);
-            Y[(int64_t)l * n_self + s] = fma(sdecay[l], z0, sforce[l] * x);
-            Y[(int64_t)(l + 8) * n_self + s] = fma(sdecay[l + 8], z1, sforce[l + 8] * x);
-        }
-        if (l < nsoe) {
-            double z = Y[(int64_t)l * n_self + s];
+        for (int l = g; l < nsoe; l += G) {
+            const double z = Y[(int64_t)l * n_self + s];
             u = fma(sw[l], z, u);
             Y[(int64_t)l * n_self + s] = fma(sdecay[l], z, sforce[l] * x);
         }
-        u += u2;
     }
     s_red[g][threadIdx.x] = u;
     __syncthreads();
     if (g == 0 && s < n_self) {
-        for (int k = 1; k < 8; k++) u += s_red[k][threadIdx.x];
+        for (int k = 1; k < G; k++) u += s_red[k][threadIdx.x];
         uself[self_tgt[s]] = u;
     }
 }
@@ -573,29 +238,48 @@ __global__ void __launch_bounds__(256) k_modes(
         if (nn.y == 0 && nn.x > 0) td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
         return;
     }
-    int sl = slot;                                                      // level n - j
-    int sll = (int)((((n - L + lag_off) % R_lag) + R_lag) % R_lag);     // level n - L - j
+    // levels n - j (ring slot sl) and n - L - j (ring_lag slot sll), j = 0..W-1, taken U at a time
+    // with all loads issued before the arithmetic (the order of the sums is j ascending)
+    int sl = slot;
+    int sll = (int)((((n - L + lag_off) % R_lag) + R_lag) % R_lag);
     double hxd, hyd, gxd, gyd;
+    constexpr int U = sizeof(T) == 8 ? 2 : 4;  // the FP64 form is bound by FP64 issue, not latency
     if constexpr (sizeof(T) == 8) {
         const double2* tp = (const double2*)(taps + (int64_t)kid * 4 * W);  // {p, q}, {pA, qA} per level
         double hx = 0, hy = 0, gx = 0, gy = 0;
-        for (int j = 0; j < W; j++) {
-            const double2 pq = tp[2 * j];
-            const double2 a = ring[(int64_t)sl * n_modes + m];
-            hx = fma(pq.x, a.x, hx);
-            hy = fma(pq.x, a.y, hy);
-            gx = fma(pq.y, a.x, gx);
-            gy = fma(pq.y, a.y, gy);
-            if (lag) {
-                const double2 pqA = tp[2 * j + 1];
-                const double2 b = ring_lag[(int64_t)sll * n_modes + m];
-                hx = fma(-pqA.x, b.x, hx);
-                hy = fma(-pqA.x, b.y, hy);
-                gx = fma(-pqA.y, b.x, gx);
-                gy = fma(-pqA.y, b.y, gy);
+        for (int j0 = 0; j0 < W; j0 += U) {
+            double2 a[U], b[U], pq[U], pqA[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int j = j0 + u;
+                if (j < W) {
+                    const int s1 = sl - u < 0 ? sl - u + R_cur : sl - u;
+                    a[u] = ring[(int64_t)s1 * n_modes + m];
+                    pq[u] = tp[2 * j];
+                    if (lag) {
+                        const int s2 = sll - u < 0 ? sll - u + R_lag : sll - u;
+                        b[u] = ring_lag[(int64_t)s2 * n_modes + m];
+                        pqA[u] = tp[2 * j + 1];
+                    }
+                }
             }
-            sl = (sl == 0) ? R_cur - 1 : sl - 1;
-            sll = (sll == 0) ? R_lag - 1 : sll - 1;
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (j0 + u < W) {
+                    hx = fma(pq[u].x, a[u].x, hx);
+                    hy = fma(pq[u].x, a[u].y, hy);
+                    gx = fma(pq[u].y, a[u].x, gx);
+                    gy = fma(pq[u].y, a[u].y, gy);
+                    if (lag) {
+                        hx = fma(-pqA[u].x, b[u].x, hx);
+                        hy = fma(-pqA[u].x, b[u].y, hy);
+                        gx = fma(-pqA[u].y, b[u].x, gx);
+                        gy = fma(-pqA[u].y, b[u].y, gy);
+                    }
+                }
+            }
+            sl = sl - U < 0 ? sl - U + R_cur : sl - U;
+            sll = sll - U < 0 ? sll - U + R_lag : sll - U;
         }
         hxd = hx, hyd = hy, gxd = gx, gyd = gy;
     } else {
@@ -603,22 +287,40 @@ __global__ void __launch_bounds__(256) k_modes(
         // the one that removes it L steps later round alike, so nothing persists in alpha
         const float4* tp = (const float4*)(taps + (int64_t)kid * 8 * W);
         float hxh = 0, hxl = 0, hyh = 0, hyl = 0, gxh = 0, gxl = 0, gyh = 0, gyl = 0;
-        for (int j = 0; j < W; j++) {
-            const float4 hi = tp[2 * j], lo = tp[2 * j + 1];
-            const float2 a = ring[(int64_t)sl * n_modes + m];
-            df_acc(hxh, hxl, hi.x, lo.x, a.x);
-            df_acc(hyh, hyl, hi.x, lo.x, a.y);
-            df_acc(gxh, gxl, hi.y, lo.y, a.x);
-            df_acc(gyh, gyl, hi.y, lo.y, a.y);
-            if (lag) {
-                const float2 b = ring_lag[(int64_t)sll * n_modes + m];
-                df_acc(hxh, hxl, -hi.z, -lo.z, b.x);
-                df_acc(hyh, hyl, -hi.z, -lo.z, b.y);
-                df_acc(gxh, gxl, -hi.w, -lo.w, b.x);
-                df_acc(gyh, gyl, -hi.w, -lo.w, b.y);
+        for (int j0 = 0; j0 < W; j0 += U) {
+            float2 a[U], b[U];
+            float4 hi[U], lo[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int j = j0 + u;
+                if (j < W) {
+                    const int s1 = sl - u < 0 ? sl - u + R_cur : sl - u;
+                    a[u] = ring[(int64_t)s1 * n_modes + m];
+                    hi[u] = tp[2 * j];
+                    lo[u] = tp[2 * j + 1];
+                    if (lag) {
+                        const int s2 = sll - u < 0 ? sll - u + R_lag : sll - u;
+                        b[u] = ring_lag[(int64_t)s2 * n_modes + m];
+                    }
+                }
             }
-            sl = (sl == 0) ? R_cur - 1 : sl - 1;
-            sll = (sll == 0) ? R_lag - 1 : sll - 1;
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (j0 + u < W) {
+                    df_acc(hxh, hxl, hi[u].x, lo[u].x, a[u].x);
+                    df_acc(hyh, hyl, hi[u].x, lo[u].x, a[u].y);
+                    df_acc(gxh, gxl, hi[u].y, lo[u].y, a[u].x);
+                    df_acc(gyh, gyl, hi[u].y, lo[u].y, a[u].y);
+                    if (lag) {
+                        df_acc(hxh, hxl, -hi[u].z, -lo[u].z, b[u].x);
+                        df_acc(hyh, hyl, -hi[u].z, -lo[u].z, b[u].y);
+                        df_acc(gxh, gxl, -hi[u].w, -lo[u].w, b[u].x);
+                        df_acc(gyh, gyl, -hi[u].w, -lo[u].w, b[u].y);
+                    }
+                }
+            }
+            sl = sl - U < 0 ? sl - U + R_cur : sl - U;
+            sll = sll - U < 0 ? sll - U + R_lag : sll - U;
         }
         hxd = (double)hxh + (double)hxl;
         hyd = (double)hyh + (double)hyl;
@@ -650,27 +352,29 @@ __global__ void __launch_bounds__(256) k_modes(
 // trapezoid interpolant of the lagged S on the grid (exp(A lam) scaling carried in the state):
 //   E_l(t_{n+1}) = r_l E_l(t_n) + f_l S_{n-L-W+1}                  (tail recurrence, one tap)
 //   alpha_F = sum_l H_l(|k|) E_l + sum_{q<W-1} Phi_q(|k|) S_{n-L-q}   (Eq. alphaFApprox + newest levels)
-// alpha_F is added to the type-2 coefficient written by k_modes.  Block (32, 8): 32 far modes x 8
+// alpha_F is added to the type-2 coefficient written by k_modes.  Block (32, G): 32 far modes x G
 // groups of terms; the W newest lagged levels of the block's modes are staged in shared memory.
+// H and Phi are stored [term][|k|], so the 32 modes of a warp (ordered by |k|) read neighbours.
+constexpr int kFarGroups = 16;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_far(const int64_t* __restrict__ d_step, int64_t n_far, int64_t n_modes, int W,
-                                             int L, int Nh, int nf, int nlam, const int* __restrict__ far_mode,
-                                             const int* __restrict__ far_k, const int2* __restrict__ mode_n,
-                                             const double* __restrict__ fac, double coef2,
-                                             const typename Cplx<T>::type* __restrict__ ring_lag, int R_lag,
-                                             int lag_off, const double* __restrict__ H, const double* __restrict__ ffir,
-                                             const double* __restrict__ fdecay, const double* __restrict__ fforce,
-                                             double2* __restrict__ B, typename Cplx<T>::type* __restrict__ td) {
+__global__ void __launch_bounds__(32 * kFarGroups) k_far(
+    const int64_t* __restrict__ d_step, int64_t n_far, int64_t n_modes, int W, int L, int Nh, int nf, int nlam,
+    int64_t n_fk, const int* __restrict__ far_mode, const int* __restrict__ far_k, const int2* __restrict__ mode_n,
+    const double* __restrict__ fac, double coef2, const typename Cplx<T>::type* __restrict__ ring_lag, int R_lag,
+    int lag_off, const double* __restrict__ H, const double* __restrict__ ffir, const double* __restrict__ fdecay,
+    const double* __restrict__ fforce, double2* __restrict__ B, typename Cplx<T>::type* __restrict__ td) {
     using C = typename Cplx<T>::type;
+    constexpr int G = kFarGroups;
     int64_t n = *d_step + 1;
     if (n - L < 1) return;
-    __shared__ double2 s_red[8][32];
+    __shared__ double2 s_red[G][32];
     __shared__ C s_S[kMaxWFar][32];
     int64_t f = (int64_t)blockIdx.x * 32 + threadIdx.x;
     int g = threadIdx.y;
     bool valid = f < n_far;
     int64_t m = valid ? far_mode[f] : 0;
-    for (int j = g; j < W; j += 8) {
+    for (int j = g; j < W; j += G) {
         int sl = (int)((((n - L - j + lag_off) % R_lag) + R_lag) % R_lag);  // level n - L - j
         C z;
         z.x = 0;
@@ -680,23 +384,22 @@ __global__ void __launch_bounds__(256) k_far(const int64_t* __restrict__ d_step,
     __syncthreads();
     double2 aF = make_double2(0.0, 0.0);
     if (valid) {
-        const int fk = far_k[f];
-        const double* Fr = ffir + (int64_t)fk * (W - 1);
-        for (int q = g; q < W - 1; q += 8) {
-            C sq = s_S[q][threadIdx.x];
-            aF.x = fma(Fr[q], (double)sq.x, aF.x);
-            aF.y = fma(Fr[q], (double)sq.y, aF.y);
+        const int64_t fk = far_k[f];
+        for (int q = g; q < W - 1; q += G) {
+            const C sq = s_S[q][threadIdx.x];
+            const double fq = ffir[(int64_t)q * n_fk + fk];
+            aF.x = fma(fq, (double)sq.x, aF.x);
+            aF.y = fma(fq, (double)sq.y, aF.y);
         }
         const C st = s_S[W - 1][threadIdx.x];
         const double sx = st.x, sy = st.y;
-        const double* Hr = H + (int64_t)fk * nlam;
-        for (int l = g; l < nlam; l += 8) {
+        for (int l = g; l < nlam; l += G) {
             double2 b = B[(int64_t)l * n_far + f];
             const double d = fdecay[l], fo = fforce[l];
             b.x = fma(d, b.x, fo * sx);
             b.y = fma(d, b.y, fo * sy);
             B[(int64_t)l * n_far + f] = b;
-            const double hl = Hr[l];
+            const double hl = H[(int64_t)l * n_fk + fk];
             aF.x = fma(hl, b.x, aF.x);
             aF.y = fma(hl, b.y, aF.y);
         }
@@ -704,7 +407,7 @@ __global__ void __launch_bounds__(256) k_far(const int64_t* __restrict__ d_step,
     s_red[g][threadIdx.x] = aF;
     __syncthreads();
     if (g == 0 && valid) {
-        for (int k = 1; k < 8; k++) {
+        for (int k = 1; k < G; k++) {
             aF.x += s_red[k][threadIdx.x].x;
             aF.y += s_red[k][threadIdx.x].y;
         }
@@ -799,17 +502,12 @@ static wfp_status output_t(Plan& pl, std::string& err) {
     ps0.stop();
     if (pl.Mt > 0) {
         ProfScope ps(pl, PP_LOCAL);
-        if (pl.NW == 32)
-            local_variant_t<T>(pl, pl.local_variant, st);
-        else
-            k_local<T><<<nblk(pl.Mt * 32, 256), 256, 0, st>>>(pl.d_step, pl.Mt, pl.d_rowptr, pl.d_col,
-                                                              (const T*)pl.d_eta, (const T*)pl.d_sigwin, pl.NW, P.nmax,
-                                                              pl.d_uloc);
+        local_run(pl, st);
         CK(cudaGetLastError());
     }
     if (pl.n_self > 0) {
         ProfScope ps(pl, PP_SELF);
-        k_self<T><<<nblk(pl.n_self, 32), dim3(32, 8), 0, st>>>(pl.d_step, pl.n_self, pl.d_self_tgt, pl.d_self_src,
+        k_self<T><<<nblk(pl.n_self, 32), dim3(32, kSelfGroups), 0, st>>>(pl.d_step, pl.n_self, pl.d_self_tgt, pl.d_self_src,
                                                                (const T*)pl.d_sigwin, pl.NW, P.W, pl.n_soe_self,
                                                                pl.d_shead, pl.d_sdecay, pl.d_sforce, pl.d_sw, pl.d_Y,
                                                                pl.d_uself);
@@ -903,11 +601,11 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err) {
     psm.stop();
     if (lag_now && P.far_active && pl.n_far > 0) {
         ProfScope ps(pl, PP_FAR);
-        dim3 blk(32, 8);
+        dim3 blk(32, kFarGroups);
         k_far<T><<<nblk(pl.n_far, 32), blk, 0, st>>>(pl.d_step, pl.n_far, pl.n_modes, P.W, P.L, P.Nh, P.nf,
-                                                      P.n_lambda, pl.d_far_mode, pl.d_far_k, pl.d_mode_n, pl.d_fac,
-                                                      coef2, (const C*)pl.d_ring_lag, pl.R_lag, pl.lag_off, pl.d_H,
-                                                      pl.d_ffir, pl.d_fdecay, pl.d_fforce, pl.d_B, (C*)pl.d_td);
+                                                      P.n_lambda, pl.n_fkappa, pl.d_far_mode, pl.d_far_k, pl.d_mode_n,
+                                                      pl.d_fac, coef2, (const C*)pl.d_ring_lag, pl.R_lag, pl.lag_off,
+                                                      pl.d_H, pl.d_ffir, pl.d_fdecay, pl.d_fforce, pl.d_B, (C*)pl.d_td);
         CK(cudaGetLastError());
     }
     // type-2: columns (C2C, inverse) then band rows (C2R); the C2R input beyond column Nh is re-zeroed
