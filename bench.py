@@ -65,13 +65,24 @@ def parse():
 
 # ----------------------------------------------------------------------------- helpers
 def dist_init():
+    """One process per GPU under torchrun (NCCL), or gloo where no GPU is visible (CPU tests)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
-        dist.init_process_group(backend=backend)
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
         return dist, int(os.environ["RANK"]), ws
     return None, 0, 1
+
+
+def max_over_ranks(dist, value: float, device=None) -> float:
+    """The slowest rank's time (the job's time under weak scaling)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 class ClockSampler:
@@ -148,7 +159,7 @@ def part_model(info: dict, M: int, Mt: int, fp64: bool) -> dict:
     nk, nl = info["n_kappa"], info["n_lambda"]
     nb, nfg, w = info["nb"], info["nf"], info["kernel_width"]
     nself, nsoe = info["n_self"], info["n_self_soe"]
-    lag = 1  # timed window is in the lagged regime
+    lag = 1 if info["lag_active"] else 0  # the timed window is in the lagged regime when there is one
     spreads = 1 + (lag and not info["lag_store"])  # a second (lagged) spread only without the stored S history
     tapw = 4 * W * s if fp64 else 8 * W * 4     # FIR taps per |k|: FP64, or FP32 hi/lo pairs
     m = {}
@@ -181,7 +192,9 @@ def run_ours(args, rank: int, world: int, dist):
         stream = torch.cuda.Stream(device=dev)
         plan0 = wfp.select_params(wl.meta["box"] / 2, wl.dt, wl.n_steps, wl.band_limit, wl.tol,
                                   precision=0 if precision == "fp64" else 1)
-        pre = plan0["L"] + plan0["W"] + 1          # reach the lagged / far-history regime
+        # reach the lagged / far-history regime when the workload has one (N_t > L); otherwise only fill
+        # the local window, so that every part the workload uses is active in the timed region
+        pre = plan0["L"] + plan0["W"] + 1 if plan0["lag_active"] else plan0["nmax"] + 1
         e2e_steps = args.e2e_steps if timed_e2e else 0
         Nt = max(wl.n_steps, pre + Wm + K + prof_steps + e2e_steps)
         t0 = time.perf_counter()
@@ -221,12 +234,9 @@ def run_ours(args, rank: int, world: int, dist):
             torch.cuda.synchronize(dev)
         n += K
         ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(dist, ms, dev)
         r = {"ms": ms, "K": K, "info": info, "plan_s": plan_s, "clocks": clk.summary(), "u_last": out.cpu().numpy(),
-             "n_last": n}
+             "n_last": n, "workload": args.config}
         # per-part timing with CUDA events on the plan's stream
         if prof_steps > 0:
             plan.profile(True)
@@ -310,7 +320,7 @@ def roofline(r: dict, M: int, Mt: int, fp64: bool) -> tuple[dict, dict]:
         if os.path.exists(tj):
             with open(tj) as f:
                 tr = json.load(f)
-            key = f"{dom}:{'fp64' if fp64 else 'mixed'}"
+            key = f"{dom}:{'fp64' if fp64 else 'mixed'}:{r['workload']}"
             ent = tr.get(key, {})
             variant_ok = dom != "local" or ent.get("local_variant") == r["info"].get("local_variant")
             if ent.get("source_hash") == source_hash(dom) and variant_ok:
@@ -437,7 +447,10 @@ def main():
         return serve(args)
     dist, rank, world = dist_init()
     if args.impl == "reference":
-        return run_reference(args, rank, world, dist)
+        run_reference(args, rank, world, dist)
+        if dist:
+            dist.destroy_process_group()
+        return
     wl, res = run_ours(args, rank, world, dist)
     if rank != 0:
         return
@@ -522,12 +535,12 @@ def run_reference(args, rank, world, dist):
     rng = np.random.default_rng(0)
     probe = max(cores, 8)
     idx = rng.choice(wl.M, probe, replace=False)
-    ev = np.column_stack([wl.src_xy[idx], np.full(probe, 900 * wl.dt)])
+    ev = np.column_stack([wl.src_xy[idx], np.full(probe, min(900, wl.n_steps) * wl.dt)])
     t0 = time.perf_counter()
     oracle.field(wl.src_xy, wl.params, ev, r_coinc=1e-12 * wl.meta["box"])
     per_eval = (time.perf_counter() - t0) / probe
     S = int(max(1, min(wl.M, 120.0 / max(1, args.steps + args.warmup) / per_eval)))
-    steps = np.linspace(800, wl.n_steps, args.steps + args.warmup).astype(int)
+    steps = np.linspace(min(800, wl.n_steps // 2), wl.n_steps, args.steps + args.warmup).astype(int)
     tot_t, tot_n = 0.0, 0
     for i, n in enumerate(steps):
         idx = rng.choice(wl.M, S, replace=False)

@@ -59,7 +59,8 @@ enum { WFP_FP64 = 0, WFP_MIXED = 1 };
  *   p             interpolation order of the local part (Sec. 6); 0 => 20, lowered (even, >= 8) so
  *                 that nmax = W + 1 + p/2 <= 32.
  *   Kf            far-history cut-off wavenumber in normalised units (Sec. 5); 0 => derived from eps.
- *   upsampfac     minimum NUFFT fine-grid upsampling factor; 0 => 1.25 (FP64) or 2.0 (MIXED).  The grid
+ *   upsampfac     minimum NUFFT fine-grid upsampling factor; 0 => 1.25 on the FP64 path; on the MIXED path
+ *                 2.0 while that keeps the grid at most 4096 points a side, else 1.25.  The grid
  *                 size n_f is the smallest 2^a, 3*2^a or 9*2^a at or above upsampfac * (2 Nh + 1).
  *   kernel_width  NUFFT spreading-kernel width in grid points; 0 => from eps and the effective
  *                 upsampling n_f / (2 Nh + 1).

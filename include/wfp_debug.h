@@ -1,10 +1,10 @@
 /*
- * wfp_debug.h -- host-only diagnostics of the 2D TK-WFP evaluator (no GPU needed).
+ * wfp_debug.h -- diagnostics of the 2D TK-WFP evaluator.
  *
- * These expose the plan-time quadrature routines that the CUDA path runs on the device, so
- * that tests on a machine without a GPU can check them against closed forms and against the
- * independent CPU oracle.  They allocate only host memory and return WFP_EINVAL on bad
- * arguments; output arrays are owned by the caller.
+ * All but the last expose the plan-time quadrature routines that the CUDA path runs on the
+ * device, so that tests on a machine without a GPU can check them against closed forms and
+ * against the independent CPU oracle; they allocate only host memory.  wfp_debug_bounded_wait
+ * runs on the GPU.  All return WFP_EINVAL on bad arguments; output arrays are owned by the caller.
  */
 #ifndef WFP_DEBUG_H
 #define WFP_DEBUG_H
@@ -50,6 +50,16 @@ wfp_status wfp_debug_soe(double lam_max, int panels, int ng, double* lam, double
  */
 wfp_status wfp_debug_hankel(double kappa, double A, double Delta, double eps, double lam_max, int panels, int ng,
                             double* H);
+
+/*
+ * The bounded wait that every mbarrier wait of the CUDA path uses (the bulk-copy pipeline of the
+ * local part), run once on the current GPU by one warp on an mbarrier of its own shared memory
+ * (no copies involved): with arrive = 0 nothing completes the barrier's phase and the wait must
+ * run out after limit_s seconds (0.001 .. 1); with arrive = 1 the phase is completed first and the
+ * wait must succeed at once.  *timed_out receives 1 if the wait ran out, *waited_s the wall time
+ * the wait took (device global timer).  Requires a GPU; WFP_ECUDA if the launch fails.
+ */
+wfp_status wfp_debug_bounded_wait(double limit_s, int arrive, int* timed_out, double* waited_s);
 
 #ifdef __cplusplus
 }

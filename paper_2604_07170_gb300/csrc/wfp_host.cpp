@@ -442,8 +442,11 @@ wfp_status select_params(double halfside, double dt, int64_t Nt, double K0, doub
     }
     P.n_lambda = P.soe_panels * P.soe_nodes;
     // NUFFT: exponential-of-semicircle kernel, width from the tolerance and upsampling factor
-    // default upsampling: 1.25 on the FP64 path (FP64 FFTs dominate there), 2 on the mixed path
-    const double sig_req = (o.upsampfac > 0) ? o.upsampfac : (P.precision == WFP_FP64 ? 1.25 : 2.0);
+    // default upsampling: 1.25 on the FP64 path (FP64 FFTs dominate there); on the mixed path 2 while
+    // the grid stays at most 4096 points a side (FP32 FFTs are cheap there and a narrower kernel
+    // saves spreading), 1.25 beyond (the FFTs dominate large grids)
+    double sig_req = o.upsampfac;
+    if (!(sig_req > 0)) sig_req = (P.precision == WFP_FP64 || 2.0 * (2 * P.Nh + 1) > 4096) ? 1.25 : 2.0;
     if (sig_req < 1.2 || sig_req > 4.0) {
         err = "upsampfac must be in [1.2, 4]";
         return WFP_EINVAL;

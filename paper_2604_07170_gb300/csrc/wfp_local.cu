@@ -3,6 +3,9 @@
 // a CSR stream of per-pair weight rows against per-source windows of the newest signal levels.
 #include <cuda_runtime.h>
 
+#include <string>
+
+#include "wfp_debug.h"
 #include "wfp_dev.h"
 #include "wfp_plan.h"
 #include "wfp_ptx.h"
@@ -315,4 +318,52 @@ void local_run(const Plan& pl, cudaStream_t st) {
     }
 }
 
+
+// one warp: wait on an mbarrier of its own shared memory with the bounded wait (see wfp_debug.h)
+__global__ void k_wait_probe(uint64_t limit_ns, int arrive, int* timed_out, unsigned long long* waited_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (arrive && threadIdx.x == 0) mbar_arrive(&bar);
+    __syncwarp();
+    const uint64_t t0 = global_ns();
+    const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+    const uint64_t t1 = global_ns();
+    if (threadIdx.x == 0) {
+        *timed_out = ok ? 0 : 1;
+        *waited_ns = (unsigned long long)(t1 - t0);
+    }
+}
+
 }  // namespace wfp
+
+extern "C" wfp_status wfp_debug_bounded_wait(double limit_s, int arrive, int* timed_out, double* waited_s) {
+    if (!timed_out || !waited_s || !(limit_s >= 1e-3 && limit_s <= 1.0)) {
+        wfp::set_error("limit_s must be in [0.001, 1] and the outputs non-NULL");
+        return WFP_EINVAL;
+    }
+    int* d_to = nullptr;
+    unsigned long long* d_w = nullptr;
+    if (cudaMalloc(&d_to, sizeof(int)) != cudaSuccess || cudaMalloc(&d_w, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaFree(d_to);
+        cudaGetLastError();
+        wfp::set_error("device allocation failed");
+        return WFP_ECUDA;
+    }
+    wfp::k_wait_probe<<<1, 32>>>((uint64_t)(limit_s * 1e9), arrive ? 1 : 0, d_to, d_w);
+    unsigned long long w = 0;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(timed_out, d_to, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&w, d_w, sizeof(w), cudaMemcpyDeviceToHost);
+    cudaFree(d_to);
+    cudaFree(d_w);
+    if (e != cudaSuccess) {
+        wfp::set_error(std::string("bounded-wait probe: ") + cudaGetErrorString(e));
+        return WFP_ECUDA;
+    }
+    *waited_s = (double)w * 1e-9;
+    return WFP_OK;
+}

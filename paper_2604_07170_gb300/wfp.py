@@ -53,7 +53,7 @@ _lib = None
 EXPORTS = ["wfp_opts_default", "wfp_plan_create", "wfp_step", "wfp_destroy", "wfp_plan_get_info",
            "wfp_step_components", "wfp_select_params", "wfp_status_string", "wfp_last_error",
            "wfp_profile", "wfp_profile_read", "wfp_local_noalloc", "wfp_debug_eta", "wfp_debug_taps", "wfp_debug_phi",
-           "wfp_debug_soe", "wfp_debug_hankel", "wfp_server_create", "wfp_server_submit", "wfp_server_tick",
+           "wfp_debug_soe", "wfp_debug_hankel", "wfp_debug_bounded_wait", "wfp_server_create", "wfp_server_submit", "wfp_server_tick",
            "wfp_server_run", "wfp_server_query", "wfp_server_result", "wfp_server_destroy"]
 
 SIGNAL_GAUSS3 = 0
@@ -107,6 +107,8 @@ def lib():
     L.wfp_debug_soe.argtypes = [_c_dbl, ctypes.c_int, ctypes.c_int, _pd, _pd]
     L.wfp_debug_hankel.argtypes = [_c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_dbl, ctypes.c_int, ctypes.c_int, _pd]
     L.wfp_debug_hankel.restype = ctypes.c_int
+    L.wfp_debug_bounded_wait.argtypes = [_c_dbl, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _pd]
+    L.wfp_debug_bounded_wait.restype = ctypes.c_int
     L.wfp_server_create.argtypes = [_c_i64, ctypes.c_int, ctypes.POINTER(wfp_opts), ctypes.POINTER(vp)]
     L.wfp_server_submit.argtypes = [vp, ctypes.POINTER(wfp_request), ctypes.POINTER(_c_i64)]
     L.wfp_server_tick.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
@@ -330,6 +332,14 @@ def debug_hankel(kappa, A, Delta, eps, lam_max=36.0, panels=20, ng=32) -> np.nda
     H = np.zeros(panels * ng)
     _check(lib().wfp_debug_hankel(kappa, A, Delta, eps, lam_max, panels, ng, _dptr(H)), "wfp_debug_hankel")
     return H
+
+
+def debug_bounded_wait(limit_s: float, arrive: bool):
+    """Run the device's bounded mbarrier wait once (GPU); returns (timed_out, waited_s)."""
+    to, w = ctypes.c_int(), _c_dbl()
+    _check(lib().wfp_debug_bounded_wait(limit_s, 1 if arrive else 0, ctypes.byref(to), ctypes.byref(w)),
+           "wfp_debug_bounded_wait")
+    return bool(to.value), w.value
 
 
 def debug_soe(lam_max, panels, ng):

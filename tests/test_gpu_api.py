@@ -188,3 +188,13 @@ def test_local_variants_give_identical_fields(precision):
     assert 1 <= info["local_variant"] <= 5
     for o in outs[1:] + [auto]:
         assert np.array_equal(outs[0], o)
+
+
+def test_bounded_device_wait_runs_out_and_reports():
+    # the wall-time bound of every mbarrier wait in the CUDA path: a phase nothing completes must
+    # make the wait give up after its limit and report it; a completed phase must pass at once
+    from paper_2604_07170_gb300 import wfp
+    timed_out, waited = wfp.debug_bounded_wait(0.2, arrive=False)
+    assert timed_out and 0.2 <= waited < 1.0
+    timed_out, waited = wfp.debug_bounded_wait(0.2, arrive=True)
+    assert not timed_out and waited < 0.01
