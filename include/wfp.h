@@ -75,8 +75,8 @@ enum { WFP_FP64 = 0, WFP_MIXED = 1 };
  *                 the stored signal history, as the paper does (Sec. 4.3); WFP_LAG_STORE keeps the
  *                 last L + W levels of S per mode in device memory; WFP_LAG_AUTO (0, default) stores
  *                 when that history takes at most 40% of the free device memory, else recomputes.
- *   spread_tile   side of the grid tile one CTA spreads onto (16 or 32); 0 => chosen at plan time by
- *                 timing both.  spread_chunk: sources staged in shared memory per round (32 or 64);
+ *   spread_tile   side of the grid tile one CTA spreads onto (8, 16 or 32); 0 => chosen at plan time
+ *                 by timing each.  spread_chunk: sources staged in shared memory per round (32 or 64);
  *                 0 => timed likewise.  Every grid point sums its sources in ascending internal order
  *                 whatever the tiling, so these choices do not change any result bit.
  *   local_variant kernel of the local part when nmax <= 32: 1 = warp-vector loads, 2..5 = weight rows

@@ -217,6 +217,8 @@ struct TileLists {
     bool made = false;
 };
 
+static int tile_slot(int ts) { return ts == 8 ? 0 : (ts == 16 ? 1 : 2); }
+
 static TileLists build_tiles(const Params& P, const std::vector<int>& soff, int ts) {
     TileLists t;
     const int ntx = P.nb / ts;
@@ -560,7 +562,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
     }
 
     // ---- NUFFT tables: footprints, kernel values, deconvolution factors, spreading tiles
-    TileLists tile_lists[2];  // tile side 16, 32
+    TileLists tile_lists[3];  // tile side 8, 16, 32
     {
         if (P.nb >= 32768) {
             err = "NUFFT band too large for 16-bit footprint offsets";
@@ -587,13 +589,14 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         // tiles of the band touched by each source footprint, for each candidate tile side; the
         // autotuner below times them and keeps one
         const int opt_ts = pl.opts.spread_tile, opt_ch = pl.opts.spread_chunk;
-        if ((opt_ts != 0 && opt_ts != 16 && opt_ts != 32) || (opt_ch != 0 && opt_ch != 32 && opt_ch != 64)) {
-            err = "spread_tile must be 0, 16 or 32 and spread_chunk 0, 32 or 64";
+        if ((opt_ts != 0 && opt_ts != 8 && opt_ts != 16 && opt_ts != 32) ||
+            (opt_ch != 0 && opt_ch != 32 && opt_ch != 64)) {
+            err = "spread_tile must be 0, 8, 16 or 32 and spread_chunk 0, 32 or 64";
             return WFP_EINVAL;
         }
-        for (int ts : {16, 32}) {
+        for (int ts : {8, 16, 32}) {
             if (opt_ts != 0 && ts != opt_ts) continue;
-            tile_lists[ts == 16 ? 0 : 1] = build_tiles(P, soff, ts);
+            tile_lists[tile_slot(ts)] = build_tiles(P, soff, ts);
         }
 
     }
@@ -713,14 +716,14 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
             int ts, ch;
         };
         std::vector<Cand> cands;
-        for (int ts : {16, 32})
-            if (tile_lists[ts == 16 ? 0 : 1].made)
+        for (int ts : {8, 16, 32})
+            if (tile_lists[tile_slot(ts)].made)
                 for (int ch : {32, 64})
                     if (pl.opts.spread_chunk == 0 || ch == pl.opts.spread_chunk) cands.push_back({ts, ch});
         size_t best = 0;
         if (cands.size() > 1) {
-            Tmp<int> txy[2], tptr[2], tsrc[2];
-            for (int i = 0; i < 2; i++)
+            Tmp<int> txy[3], tptr[3], tsrc[3];
+            for (int i = 0; i < 3; i++)
                 if (tile_lists[i].made) {
                     CK(upload_tmp(txy[i], tile_lists[i].txy));
                     CK(upload_tmp(tptr[i], tile_lists[i].tptr));
@@ -731,7 +734,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
             CK(cudaEventCreate(&e1));
             float best_ms = 1e30f;
             for (size_t c = 0; c < cands.size(); c++) {
-                const int i = cands[c].ts == 16 ? 0 : 1;
+                const int i = tile_slot(cands[c].ts);
                 const int nt = (int)tile_lists[i].txy.size();
                 for (int r = 0; r < 7; r++) {
                     if (r == 2) cudaEventRecord(e0, pl.stream);
@@ -755,7 +758,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         }
         pl.spread_ts = cands[best].ts;
         pl.spread_ch = cands[best].ch;
-        const TileLists& tl = tile_lists[pl.spread_ts == 16 ? 0 : 1];
+        const TileLists& tl = tile_lists[tile_slot(pl.spread_ts)];
         pl.n_tiles = (int)tl.txy.size();
         CK(upload(mem, &pl.d_tile_xy, tl.txy));
         CK(upload(mem, &pl.d_tile_ptr, tl.tptr));

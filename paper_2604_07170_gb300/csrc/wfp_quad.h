@@ -125,7 +125,7 @@ WFP_HD inline double sin_over(double k, double x) {
 // s nodes (sq, wq on [0, dt]) and phi', phi'' at s + m dt (f1, f2: [W][ngt]) are precomputed.
 // rot = {cos(kappa dt), sin(kappa dt)/kappa, kappa sin(kappa dt)}.
 // Tap writers: planar [p | q | pA | qA] (W each, FP64), or interleaved per level m: FP64
-// {p, q, pA, qA}, FP32 {p, q, pA, qA} rounded followed by their rounding residuals (hi/lo pairs).
+// {p, q, pA, qA}; FP32 hi/lo pairs (rounded value and its rounding residual) grouped by FIR.
 struct TapsPlanar {
     double* t;
     int W;
@@ -151,13 +151,16 @@ struct TapsInterleaved<double> {
 template <>
 struct TapsInterleaved<float> {
     float* t;
+    // per level: {p, pA} hi, {p, pA} lo, {q, qA} hi, {q, qA} lo -- one float4 per FIR (h or g)
     WFP_HD void operator()(int m, double p, double q, double pa, double qa) const {
-        const double v[4] = {p, q, pa, qa};
-        for (int i = 0; i < 4; i++) {
-            float hi = (float)v[i];
-            t[8 * m + i] = hi;
-            t[8 * m + 4 + i] = (float)(v[i] - (double)hi);
-        }
+        const double v[4] = {p, pa, q, qa};
+        for (int i = 0; i < 2; i++)
+            for (int k = 0; k < 2; k++) {
+                const double x = v[2 * i + k];
+                const float hi = (float)x;
+                t[8 * m + 4 * i + k] = hi;
+                t[8 * m + 4 * i + 2 + k] = (float)(x - (double)hi);
+            }
     }
 };
 

@@ -172,7 +172,9 @@ static void spread_one(const Plan& pl, int lag, int n_tiles, const int* txy, con
 template <typename T>
 static void spread_t(const Plan& pl, int ts, int ch, int lag, int n_tiles, const int* txy, const int* tptr,
                      const int* tsrc, T* sp, cudaStream_t st) {
-    if (ts == 16)
+    if (ts == 8)
+        (ch == 32 ? spread_one<T, 8, 32> : spread_one<T, 8, 64>)(pl, lag, n_tiles, txy, tptr, tsrc, sp, st);
+    else if (ts == 16)
         (ch == 32 ? spread_one<T, 16, 32> : spread_one<T, 16, 64>)(pl, lag, n_tiles, txy, tptr, tsrc, sp, st);
     else
         (ch == 32 ? spread_one<T, 32, 32> : spread_one<T, 32, 64>)(pl, lag, n_tiles, txy, tptr, tsrc, sp, st);
@@ -283,49 +285,7 @@ __global__ void __launch_bounds__(256) k_modes(
         }
         hxd = hx, hyd = hy, gxd = gx, gyd = gy;
     } else {
-        // hi/lo taps and error-free products summed in double-float: the FIR that adds a level and
-        // the one that removes it L steps later round alike, so nothing persists in alpha
-        const float4* tp = (const float4*)(taps + (int64_t)kid * 8 * W);
-        float hxh = 0, hxl = 0, hyh = 0, hyl = 0, gxh = 0, gxl = 0, gyh = 0, gyl = 0;
-        for (int j0 = 0; j0 < W; j0 += U) {
-            float2 a[U], b[U];
-            float4 hi[U], lo[U];
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                const int j = j0 + u;
-                if (j < W) {
-                    const int s1 = sl - u < 0 ? sl - u + R_cur : sl - u;
-                    a[u] = ring[(int64_t)s1 * n_modes + m];
-                    hi[u] = tp[2 * j];
-                    lo[u] = tp[2 * j + 1];
-                    if (lag) {
-                        const int s2 = sll - u < 0 ? sll - u + R_lag : sll - u;
-                        b[u] = ring_lag[(int64_t)s2 * n_modes + m];
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                if (j0 + u < W) {
-                    df_acc(hxh, hxl, hi[u].x, lo[u].x, a[u].x);
-                    df_acc(hyh, hyl, hi[u].x, lo[u].x, a[u].y);
-                    df_acc(gxh, gxl, hi[u].y, lo[u].y, a[u].x);
-                    df_acc(gyh, gyl, hi[u].y, lo[u].y, a[u].y);
-                    if (lag) {
-                        df_acc(hxh, hxl, -hi[u].z, -lo[u].z, b[u].x);
-                        df_acc(hyh, hyl, -hi[u].z, -lo[u].z, b[u].y);
-                        df_acc(gxh, gxl, -hi[u].w, -lo[u].w, b[u].x);
-                        df_acc(gyh, gyl, -hi[u].w, -lo[u].w, b[u].y);
-                    }
-                }
-            }
-            sl = sl - U < 0 ? sl - U + R_cur : sl - U;
-            sll = sll - U < 0 ? sll - U + R_lag : sll - U;
-        }
-        hxd = (double)hxh + (double)hxl;
-        hyd = (double)hyh + (double)hyl;
-        gxd = (double)gxh + (double)gxl;
-        gyd = (double)gyh + (double)gyl;
+        static_assert(sizeof(T) == 8, "the FP32 mode update is k_modes_pair");
     }
     double c = rot[3 * kid], sk = rot[3 * kid + 1], ks = rot[3 * kid + 2];
     double2 a = alpha[m], ad = alphad[m];
@@ -344,6 +304,129 @@ __global__ void __launch_bounds__(256) k_modes(
     if (nn.y == 0 && nn.x > 0) {
         o.y = (T)(an.y * cf);
         td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
+    }
+}
+
+// Mixed-path mode update: two threads per mode.  Thread r = 0 forms h, r = 1 forms g (Eq. hggrid)
+// from its half of the taps (hi/lo pairs, one float4 per level) with error-free products summed in
+// double-float, so that the FIR adding a level and the one removing it L steps later round alike
+// and nothing persists in alpha.  The newest current and lagged levels come from registers.
+// Thread 0 advances alpha with h and writes the type-2 coefficient, thread 1 advances alpha-dot
+// with g (Eq. alphakEvolution, FP64).
+__global__ void __launch_bounds__(256) k_modes_pair(
+    const int64_t* __restrict__ d_step, int64_t n_modes, int W, int L, int Nh, int nf, const int2* __restrict__ mode_n,
+    const int* __restrict__ mode_k, const double* __restrict__ fac, double coef2, const float2* __restrict__ tc_cur,
+    const float2* __restrict__ tc_lag, float2* __restrict__ ring, float2* __restrict__ ring_lag, int R_cur, int R_lag,
+    int lag_off, int write_lag, const float* __restrict__ taps, const double* __restrict__ rot,
+    double2* __restrict__ alpha, double2* __restrict__ alphad, float2* __restrict__ td, int64_t near_sq) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t m = tid >> 1;
+    const int r = (int)(tid & 1);
+    const bool valid = m < n_modes;
+    const int64_t n = *d_step + 1;
+    const bool lag = (n - L >= 1);
+    int2 nn = make_int2(0, 0);
+    int kid = 0;
+    int64_t gi = 0;
+    double f = 0.0;
+    float2 s_cur = make_float2(0.f, 0.f), s_lag = make_float2(0.f, 0.f);
+    const int slot = (int)(n % R_cur);
+    const int slot_lag = (int)((((n - L + lag_off) % R_lag) + R_lag) % R_lag);  // level n - L
+    if (valid) {
+        nn = mode_n[m];
+        kid = mode_k[m];
+        const int row = nn.x < 0 ? nn.x + nf : nn.x;
+        gi = (int64_t)row * (Nh + 1) + nn.y;
+        f = fac[nn.x < 0 ? -nn.x : nn.x] * fac[nn.y];
+        const float2 t = tc_cur[gi];
+        s_cur.x = (float)((double)t.x * f);
+        s_cur.y = (float)(-(double)t.y * f);
+        if (r == 0) ring[(int64_t)slot * n_modes + m] = s_cur;
+        if (lag) {
+            if (write_lag) {  // lagged NUFFT result: level n - L
+                const float2 u = tc_lag[gi];
+                s_lag.x = (float)((double)u.x * f);
+                s_lag.y = (float)(-(double)u.y * f);
+                if (r == 1) ring_lag[(int64_t)slot_lag * n_modes + m] = s_lag;
+            } else {
+                s_lag = ring_lag[(int64_t)slot_lag * n_modes + m];
+            }
+        }
+    }
+    // near history truncated at |k| <= K (Eq. uhtraptrunc): modes beyond carry only S
+    const bool near = valid && (int64_t)nn.x * nn.x + (int64_t)nn.y * nn.y <= near_sq;
+    float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f;
+    if (near) {
+        const float4* tp = (const float4*)(taps + (int64_t)kid * 8 * W) + r;  // this thread's FIR
+        constexpr int U = 4;
+        int sl = slot, sll = slot_lag;
+        for (int j0 = 0; j0 < W; j0 += U) {
+            float2 a[U], b[U];
+            float4 t4[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int j = j0 + u;
+                if (j < W) {
+                    t4[u] = tp[2 * j];
+                    if (j == 0) {
+                        a[u] = s_cur;
+                        b[u] = s_lag;
+                    } else {
+                        const int s1 = sl - u < 0 ? sl - u + R_cur : sl - u;
+                        a[u] = ring[(int64_t)s1 * n_modes + m];
+                        if (lag) {
+                            const int s2 = sll - u < 0 ? sll - u + R_lag : sll - u;
+                            b[u] = ring_lag[(int64_t)s2 * n_modes + m];
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (j0 + u < W) {
+                    df_acc(xh, xl, t4[u].x, t4[u].z, a[u].x);
+                    df_acc(yh, yl, t4[u].x, t4[u].z, a[u].y);
+                    if (lag) {
+                        df_acc(xh, xl, -t4[u].y, -t4[u].w, b[u].x);
+                        df_acc(yh, yl, -t4[u].y, -t4[u].w, b[u].y);
+                    }
+                }
+            }
+            sl = sl - U < 0 ? sl - U + R_cur : sl - U;
+            sll = sll - U < 0 ? sll - U + R_lag : sll - U;
+        }
+    }
+    const double vx = (double)xh + (double)xl, vy = (double)yh + (double)yl;  // h (r = 0) or g (r = 1)
+    if (!valid) return;
+    if (!near) {
+        if (r == 0) {
+            float2 o = make_float2(0.f, 0.f);
+            td[gi] = o;
+            if (nn.y == 0 && nn.x > 0) td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
+        }
+        return;
+    }
+    const double c = rot[3 * kid], sk = rot[3 * kid + 1], ks = rot[3 * kid + 2];
+    const double2 a = alpha[m], ad = alphad[m];
+    if (r == 0) {  // alpha(t + dt) = cos(k dt) alpha + sin(k dt)/k alphadot + h
+        double2 an;
+        an.x = fma(c, a.x, fma(sk, ad.x, vx));
+        an.y = fma(c, a.y, fma(sk, ad.y, vy));
+        alpha[m] = an;
+        const double cf = coef2 * f;
+        float2 o;
+        o.x = (float)(an.x * cf);
+        o.y = (float)(-an.y * cf);
+        td[gi] = o;
+        if (nn.y == 0 && nn.x > 0) {
+            o.y = (float)(an.y * cf);
+            td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
+        }
+    } else {  // alphadot(t + dt) = -k sin(k dt) alpha + cos(k dt) alphadot + g
+        double2 adn;
+        adn.x = fma(-ks, a.x, fma(c, ad.x, vx));
+        adn.y = fma(-ks, a.y, fma(c, ad.y, vy));
+        alphad[m] = adn;
     }
 }
 
@@ -592,11 +675,20 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err) {
     psf.stop();
     double coef2 = (P.dk / (2 * kPi)) * (P.dk / (2 * kPi));
     ProfScope psm(pl, PP_MODES);
-    k_modes<T><<<nblk(pl.n_modes, 256), 256, 0, st>>>(
-        pl.d_step, pl.n_modes, P.W, P.L, P.Nh, P.nf, pl.d_mode_n, pl.d_mode_k, pl.d_fac, coef2, (const C*)pl.d_tc_cur,
-        (const C*)pl.d_tc_lag, (C*)pl.d_ring, (C*)pl.d_ring_lag, pl.R_cur, pl.R_lag, pl.lag_off, pl.lag_store ? 0 : 1,
-        (const T*)pl.d_taps, pl.d_rot, pl.d_alpha,
-        pl.d_alphad, (C*)pl.d_td, (int64_t)std::floor((P.K / P.dk) * (P.K / P.dk)));
+    const int64_t near_sq = (int64_t)std::floor((P.K / P.dk) * (P.K / P.dk));
+    if constexpr (sizeof(T) == 8) {
+        k_modes<T><<<nblk(pl.n_modes, 256), 256, 0, st>>>(
+            pl.d_step, pl.n_modes, P.W, P.L, P.Nh, P.nf, pl.d_mode_n, pl.d_mode_k, pl.d_fac, coef2,
+            (const C*)pl.d_tc_cur, (const C*)pl.d_tc_lag, (C*)pl.d_ring, (C*)pl.d_ring_lag, pl.R_cur, pl.R_lag,
+            pl.lag_off, pl.lag_store ? 0 : 1, (const T*)pl.d_taps, pl.d_rot, pl.d_alpha, pl.d_alphad, (C*)pl.d_td,
+            near_sq);
+    } else {
+        k_modes_pair<<<nblk(2 * pl.n_modes, 256), 256, 0, st>>>(
+            pl.d_step, pl.n_modes, P.W, P.L, P.Nh, P.nf, pl.d_mode_n, pl.d_mode_k, pl.d_fac, coef2,
+            (const float2*)pl.d_tc_cur, (const float2*)pl.d_tc_lag, (float2*)pl.d_ring, (float2*)pl.d_ring_lag,
+            pl.R_cur, pl.R_lag, pl.lag_off, pl.lag_store ? 0 : 1, (const float*)pl.d_taps, pl.d_rot, pl.d_alpha,
+            pl.d_alphad, (float2*)pl.d_td, near_sq);
+    }
     CK(cudaGetLastError());
     psm.stop();
     if (lag_now && P.far_active && pl.n_far > 0) {

@@ -164,12 +164,12 @@ def test_spreading_tilings_give_identical_fields():
     # so the autotuner's choice cannot change a bit of the result
     wl = inputs.small(300, 4.0, 120, seed=19, curve=True)
     outs = []
-    for ts, ch in ((16, 32), (16, 64), (32, 32), (32, 64)):
+    for ts, ch in ((8, 32), (8, 64), (16, 32), (16, 64), (32, 32), (32, 64)):
         o, info = _run(wl, 120, spread_tile=ts, spread_chunk=ch)
         assert info["spread_tile"] == ts and info["spread_chunk"] == ch
         outs.append(o)
     auto, info = _run(wl, 120)
-    assert info["spread_tile"] in (16, 32) and info["spread_chunk"] in (32, 64)
+    assert info["spread_tile"] in (8, 16, 32) and info["spread_chunk"] in (32, 64)
     for o in outs[1:] + [auto]:
         assert np.array_equal(outs[0], o)
 
