@@ -82,6 +82,10 @@ enum { WFP_FP64 = 0, WFP_MIXED = 1 };
  *   local_variant kernel of the local part when nmax <= 32: 1 = warp-vector loads, 2..5 = weight rows
  *                 staged into shared memory by bulk asynchronous copies (four stage/CTA shapes);
  *                 0 => the fastest, timed at plan time.  All variants give the same bits.
+ *   local_interp  interpolant of the signal inside the local quadrature (Sec. 6): WFP_INTERP_HYBRID
+ *                 (0, default) fits the newest four intervals by band-limited least squares and uses
+ *                 p-point Lagrange elsewhere; WFP_INTERP_LAGRANGE uses p-point Lagrange on the p nearest
+ *                 grid values everywhere, as the paper does (order-p convergence, Sec. 7).
  */
 typedef struct {
     int precision;
@@ -99,7 +103,10 @@ typedef struct {
     int spread_tile;
     int spread_chunk;
     int local_variant;
+    int local_interp;
 } wfp_opts;
+
+enum { WFP_INTERP_HYBRID = 0, WFP_INTERP_LAGRANGE = 1 };
 
 enum { WFP_LAG_AUTO = 0, WFP_LAG_RECOMPUTE = 1, WFP_LAG_STORE = 2 };
 
@@ -202,6 +209,24 @@ wfp_status wfp_select_params(double halfside, double dt, int64_t Nt, double band
                              const wfp_opts* opts, wfp_info* info);
 
 /*
+ * Checkpoint and resume.  The state a plan carries from step to step -- the step count, the
+ * signal windows and history, the stored S levels, the mode amplitudes alpha and alpha-dot
+ * (Sec. 4), the far-history and self-term recurrence states (Sec. 5) and the near-history field
+ * u_h left for the next step -- is written to, or read from, a caller-owned host buffer.
+ *   wfp_checkpoint_size: *bytes receives the buffer size the plan needs.
+ *   wfp_checkpoint_save: synchronises the plan's stream and copies the state into buf (bytes >= size).
+ *   wfp_checkpoint_load: copies a saved state into a plan created from the same inputs and options
+ *                        (checked against a fingerprint of the derived parameters and sizes; a
+ *                        mismatch returns WFP_EINVAL and leaves the plan unchanged).  Stepping then
+ *                        continues from the saved step and gives the same bits as the plan that was
+ *                        saved.
+ * Errors: WFP_EINVAL (NULL, short buffer, mismatch), WFP_ESTATE (poisoned plan), WFP_ECUDA.
+ */
+wfp_status wfp_checkpoint_size(wfp_plan plan, int64_t* bytes);
+wfp_status wfp_checkpoint_save(wfp_plan plan, void* buf, int64_t bytes);
+wfp_status wfp_checkpoint_load(wfp_plan plan, const void* buf, int64_t bytes);
+
+/*
  * Local part of one step without any allocation (the paper has no counterpart: this entry point
  * exists for callers that cannot allocate memory when they need the result -- code running
  * while a CUDA stream is captured into a graph, where cudaMalloc cannot be captured; code whose
@@ -254,8 +279,11 @@ typedef struct wfp_server_s* wfp_server;
 /* Signal families generated on the device.
  * WFP_SIGNAL_GAUSS3: 8 doubles per source [a1 a2 a3 c1 c2 c3 s w],
  *   sigma_j(t) = sum_q a_q exp(-(t - c_q)^2 / (2 s^2)) sin(w (t - c_q)) for t > 0, 0 for t <= 0
- *   (Gaussian-modulated pulses, the kind of signals of the paper's examples, Sec. 7). */
-enum { WFP_SIGNAL_GAUSS3 = 0 };
+ *   (Gaussian-modulated pulses).
+ * WFP_SIGNAL_ERF: 2 doubles per source [t0 w],
+ *   sigma_j(t) = 0.5 (erf(5 (t - t0)) + 1) sin(w (t - t0)) for t > 0, 0 for t <= 0
+ *   (the switched sines of the paper's examples, Sec. 7, Eq. exampleDensities). */
+enum { WFP_SIGNAL_GAUSS3 = 0, WFP_SIGNAL_ERF = 1 };
 
 typedef struct {
     int64_t M;                    /* sources (>= 1) */
@@ -266,8 +294,8 @@ typedef struct {
     int64_t Nt;
     double band_limit;
     double tol;
-    int signal_family;            /* WFP_SIGNAL_GAUSS3 */
-    const double* signal_params;  /* host, 8*M doubles; copied */
+    int signal_family;            /* WFP_SIGNAL_GAUSS3 or WFP_SIGNAL_ERF */
+    const double* signal_params;  /* host, 8*M (GAUSS3) or 2*M (ERF) doubles; copied */
     int n_out;                    /* number of output steps; 0 => the final step N_t only */
     const int64_t* out_steps;     /* host, n_out step indices in 1..N_t (any order; kept sorted) */
 } wfp_request;

@@ -379,6 +379,10 @@ wfp_status select_params(double halfside, double dt, int64_t Nt, double K0, doub
         err = "precision must be WFP_FP64 or WFP_MIXED";
         return WFP_EINVAL;
     }
+    if (o.local_interp != WFP_INTERP_HYBRID && o.local_interp != WFP_INTERP_LAGRANGE) {
+        err = "local_interp must be WFP_INTERP_HYBRID or WFP_INTERP_LAGRANGE";
+        return WFP_EINVAL;
+    }
     P.precision = o.precision;
     P.exclude_self = o.exclude_self != 0;
     P.scale = 1.0 / halfside;

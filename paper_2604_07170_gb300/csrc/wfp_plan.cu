@@ -352,7 +352,9 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         pl.d_eta = eta;
         if (pl.n_slots > 0) {
             k_eta<T><<<nblk(pl.n_slots, 128), 128>>>(pl.n_slots, d_r.p, P.dt, P.W, P.p, P.nmax, pl.NW, pl.d_phicoef,
-                                                     d_gx.p, d_gw.p, ng, d_wl.p, d_bls.p, eta);
+                                                     d_gx.p, d_gw.p, ng, d_wl.p,
+                                                     pl.opts.local_interp == WFP_INTERP_LAGRANGE ? nullptr : d_bls.p,
+                                                     eta);
             CK(cudaGetLastError());
         }
         CK(cudaDeviceSynchronize());

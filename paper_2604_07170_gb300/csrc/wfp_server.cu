@@ -51,6 +51,17 @@ __global__ void k_gen_gauss3(int64_t M, const double* __restrict__ par, double t
     out[j] = v;
 }
 
+// sigma_j(t) = 0.5 (erf(5 (t - t0)) + 1) sin(w (t - t0)) for t > 0, zero for t <= 0 (the switched
+// sines of the paper's examples, Sec. 7); params per source [t0 w]
+__global__ void k_gen_erf(int64_t M, const double* __restrict__ par, double t, double* __restrict__ out) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const double z = t - par[2 * j];
+    out[j] = (t > 0.0) ? 0.5 * (erf(5.0 * z) + 1.0) * sin(par[2 * j + 1] * z) : 0.0;
+}
+
+static int params_per_source(int family) { return family == WFP_SIGNAL_ERF ? 2 : 8; }
+
 struct Request {
     int64_t id = 0;
     std::vector<double> src, tgt, par;
@@ -242,7 +253,8 @@ wfp_status wfp_server_submit(wfp_server sv, const wfp_request* q, int64_t* id) {
     if (q->M < 1 || q->Mt < 1 || !q->src_xy || !q->signal_params || q->Nt < 1 || q->n_out < 0 ||
         (q->n_out > 0 && !q->out_steps))
         return sfail(WFP_EINVAL, "bad request");
-    if (q->signal_family != WFP_SIGNAL_GAUSS3) return sfail(WFP_EUNSUPPORTED, "unknown signal family");
+    if (q->signal_family != WFP_SIGNAL_GAUSS3 && q->signal_family != WFP_SIGNAL_ERF)
+        return sfail(WFP_EUNSUPPORTED, "unknown signal family");
     auto r = std::make_unique<Request>();
     r->id = sv->next_id++;
     r->M = q->M;
@@ -250,7 +262,7 @@ wfp_status wfp_server_submit(wfp_server sv, const wfp_request* q, int64_t* id) {
     r->src.assign(q->src_xy, q->src_xy + 2 * q->M);
     const double* t = q->tgt_xy ? q->tgt_xy : q->src_xy;
     r->tgt.assign(t, t + 2 * q->Mt);
-    r->par.assign(q->signal_params, q->signal_params + 8 * q->M);
+    r->par.assign(q->signal_params, q->signal_params + params_per_source(q->signal_family) * q->M);
     r->dt = q->dt;
     r->Nt = q->Nt;
     r->K0 = q->band_limit;
@@ -327,7 +339,11 @@ wfp_status wfp_server_tick(wfp_server sv, int* n_active, int* n_pending) {
             r->state = WFP_REQ_FAILED;
             continue;
         }
-        k_gen_gauss3<<<(unsigned)((r->M + 255) / 256), 256, 0, pl.stream>>>(r->M, r->d_par, n * r->dt, pl.d_sig_in);
+        if (r->family == WFP_SIGNAL_ERF)
+            k_gen_erf<<<(unsigned)((r->M + 255) / 256), 256, 0, pl.stream>>>(r->M, r->d_par, n * r->dt, pl.d_sig_in);
+        else
+            k_gen_gauss3<<<(unsigned)((r->M + 255) / 256), 256, 0, pl.stream>>>(r->M, r->d_par, n * r->dt,
+                                                                                 pl.d_sig_in);
         double* dst = nullptr;
         auto pos = std::lower_bound(r->out_steps.begin(), r->out_steps.end(), n);
         if (pos != r->out_steps.end() && *pos == n) dst = r->d_out + (pos - r->out_steps.begin()) * r->Mt;

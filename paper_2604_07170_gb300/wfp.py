@@ -16,6 +16,7 @@ from . import build as _build
 WFP_OK, WFP_EINVAL, WFP_ENOMEM, WFP_ECUDA, WFP_ESTATE, WFP_ETIMEOUT, WFP_EUNSUPPORTED = range(7)
 FP64, MIXED = 0, 1
 LAG_AUTO, LAG_RECOMPUTE, LAG_STORE = 0, 1, 2
+INTERP_HYBRID, INTERP_LAGRANGE = 0, 1
 
 _c_i64 = ctypes.c_int64
 _c_dbl = ctypes.c_double
@@ -27,7 +28,7 @@ class wfp_opts(ctypes.Structure):
                 ("Kf", _c_dbl), ("upsampfac", _c_dbl), ("kernel_width", ctypes.c_int),
                 ("soe_nodes", ctypes.c_int), ("exclude_self", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("use_graph", ctypes.c_int), ("lag_mode", ctypes.c_int), ("spread_tile", ctypes.c_int),
-                ("spread_chunk", ctypes.c_int), ("local_variant", ctypes.c_int)]
+                ("spread_chunk", ctypes.c_int), ("local_variant", ctypes.c_int), ("local_interp", ctypes.c_int)]
 
 
 class wfp_info(ctypes.Structure):
@@ -53,10 +54,11 @@ _lib = None
 EXPORTS = ["wfp_opts_default", "wfp_plan_create", "wfp_step", "wfp_destroy", "wfp_plan_get_info",
            "wfp_step_components", "wfp_select_params", "wfp_status_string", "wfp_last_error",
            "wfp_profile", "wfp_profile_read", "wfp_local_noalloc", "wfp_debug_eta", "wfp_debug_taps", "wfp_debug_phi",
-           "wfp_debug_soe", "wfp_debug_hankel", "wfp_debug_bounded_wait", "wfp_server_create", "wfp_server_submit", "wfp_server_tick",
+           "wfp_debug_soe", "wfp_debug_hankel", "wfp_debug_bounded_wait", "wfp_checkpoint_size",
+           "wfp_checkpoint_save", "wfp_checkpoint_load", "wfp_server_create", "wfp_server_submit", "wfp_server_tick",
            "wfp_server_run", "wfp_server_query", "wfp_server_result", "wfp_server_destroy"]
 
-SIGNAL_GAUSS3 = 0
+SIGNAL_GAUSS3, SIGNAL_ERF = 0, 1
 REQ_PENDING, REQ_ACTIVE, REQ_DONE, REQ_FAILED = range(4)
 
 
@@ -107,6 +109,11 @@ def lib():
     L.wfp_debug_soe.argtypes = [_c_dbl, ctypes.c_int, ctypes.c_int, _pd, _pd]
     L.wfp_debug_hankel.argtypes = [_c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_dbl, ctypes.c_int, ctypes.c_int, _pd]
     L.wfp_debug_hankel.restype = ctypes.c_int
+    L.wfp_checkpoint_size.argtypes = [vp, ctypes.POINTER(_c_i64)]
+    L.wfp_checkpoint_save.argtypes = [vp, vp, _c_i64]
+    L.wfp_checkpoint_load.argtypes = [vp, vp, _c_i64]
+    for name in ("wfp_checkpoint_size", "wfp_checkpoint_save", "wfp_checkpoint_load"):
+        getattr(L, name).restype = ctypes.c_int
     L.wfp_debug_bounded_wait.argtypes = [_c_dbl, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _pd]
     L.wfp_debug_bounded_wait.restype = ctypes.c_int
     L.wfp_server_create.argtypes = [_c_i64, ctypes.c_int, ctypes.POINTER(wfp_opts), ctypes.POINTER(vp)]
@@ -212,6 +219,20 @@ class Plan:
                                       ctypes.byref(k)), "wfp_profile_read")
         return {names[i].decode(): (float(ms[i]), int(cnt[i])) for i in range(min(k.value, n))}
 
+    def checkpoint(self) -> np.ndarray:
+        """The plan's step-to-step state as a host byte array (wfp_checkpoint_save)."""
+        n = _c_i64()
+        _check(lib().wfp_checkpoint_size(self._h, ctypes.byref(n)), "wfp_checkpoint_size")
+        buf = np.empty(n.value, dtype=np.uint8)
+        _check(lib().wfp_checkpoint_save(self._h, buf.ctypes.data_as(ctypes.c_void_p), n.value), "wfp_checkpoint_save")
+        return buf
+
+    def restore(self, buf: np.ndarray):
+        """Continue from a state saved by a plan of the same inputs and options (wfp_checkpoint_load)."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(lib().wfp_checkpoint_load(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.size),
+               "wfp_checkpoint_load")
+
     def info(self) -> dict:
         i = wfp_info()
         _check(lib().wfp_plan_get_info(self._h, ctypes.byref(i)), "wfp_plan_get_info")
@@ -257,15 +278,15 @@ class Server:
         self._h = h
 
     def submit(self, src_xy, signal_params, dt: float, Nt: int, band_limit: float, tol: float = 1e-6,
-               tgt_xy=None, out_steps=None) -> int:
+               tgt_xy=None, out_steps=None, family: int = SIGNAL_GAUSS3) -> int:
         src = np.ascontiguousarray(src_xy, dtype=np.float64)
         par = np.ascontiguousarray(signal_params, dtype=np.float64)
-        assert par.shape == (src.shape[0], 8)
+        assert par.shape == (src.shape[0], 2 if family == SIGNAL_ERF else 8)
         tgt = None if tgt_xy is None else np.ascontiguousarray(tgt_xy, dtype=np.float64)
         steps = None if out_steps is None else np.ascontiguousarray(out_steps, dtype=np.int64)
         q = wfp_request(M=src.shape[0], src_xy=_dptr(src), Mt=(src if tgt is None else tgt).shape[0],
                         tgt_xy=None if tgt is None else _dptr(tgt), dt=dt, Nt=int(Nt), band_limit=band_limit,
-                        tol=tol, signal_family=SIGNAL_GAUSS3, signal_params=_dptr(par),
+                        tol=tol, signal_family=family, signal_params=_dptr(par),
                         n_out=0 if steps is None else steps.size,
                         out_steps=None if steps is None else steps.ctypes.data_as(ctypes.POINTER(_c_i64)))
         rid = _c_i64()

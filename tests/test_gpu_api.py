@@ -198,3 +198,31 @@ def test_bounded_device_wait_runs_out_and_reports():
     assert timed_out and 0.2 <= waited < 1.0
     timed_out, waited = wfp.debug_bounded_wait(0.2, arrive=True)
     assert not timed_out and waited < 0.01
+
+
+@pytest.mark.parametrize("precision,lag_mode", [(0, 2), (1, 2), (0, 1)])
+def test_checkpoint_resume_gives_the_same_bits(precision, lag_mode):
+    # save mid-run (lagged S and far history active), resume in a fresh plan of the same inputs
+    from paper_2604_07170_gb300 import wfp
+    wl = inputs.small(120, 3.0, 220, seed=21)
+    sig = wl.sigma(1, 221)
+    kw = dict(precision=precision, lag_mode=lag_mode)
+    a = wfp.Plan(wl.src_xy, None, wl.dt, wl.n_steps, wl.band_limit, wl.tol, **kw)
+    for n in range(150):
+        a.step(sig[n])
+    assert a.info()["lag_active"]
+    ck = a.checkpoint()
+    ref = np.stack([a.step(sig[n]) for n in range(150, 220)])
+    a.close()
+    b = wfp.Plan(wl.src_xy, None, wl.dt, wl.n_steps, wl.band_limit, wl.tol, **kw)
+    b.restore(ck)
+    got = np.stack([b.step(sig[n]) for n in range(150, 220)])
+    b.close()
+    assert np.array_equal(ref, got)
+    # a plan of other inputs refuses the state and stays usable
+    c = wfp.Plan(wl.src_xy, None, wl.dt, wl.n_steps + 1, wl.band_limit, wl.tol, **kw)
+    with pytest.raises(wfp.WFPError) as ei:
+        c.restore(ck)
+    assert ei.value.code == wfp.WFP_EINVAL
+    c.step(sig[0])
+    c.close()
