@@ -3,6 +3,7 @@
 // a CSR stream of per-pair weight rows against per-source windows of the newest signal levels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <string>
 
 #include "wfp_debug.h"
@@ -152,12 +153,14 @@ __global__ void __launch_bounds__(256) k_local_vec(int64_t Mt, const int64_t* __
 }
 
 // Local part with the weight stream staged by bulk asynchronous copies (the form used on sm_103a
-// for nmax <= 32).  Each warp owns one target row: lane 0 keeps S stages of CH pair slots (their
-// weight rows and source indices, contiguous in HBM) in flight into a per-warp shared-memory ring,
-// each stage completed on its own mbarrier; the lanes consume a stage as in k_local_vec (weights
-// from shared memory, windows gathered from L2) and lane 0 refills the buffer with the stage S
-// ahead.  Rows are padded to multiples of 4 slots, so every copy is 16-byte aligned and sized.
-// A wait that runs out sets *err (host-mapped) and the warp drains its copies and returns.
+// for nmax <= 32).  A persistent grid (as many CTAs as fit at once) whose warps take target rows
+// from a counter: lane 0 keeps S stages of CH pair slots of the row (their weight rows and source
+// indices, contiguous in HBM) in flight into a per-warp shared-memory ring, each stage completed on
+// its own mbarrier; the lanes consume a stage as in k_local_vec (weights from shared memory,
+// windows gathered from L2) and lane 0 refills the buffer with the stage S ahead.  Rows are padded
+// to multiples of 4 slots, so every copy is 16-byte aligned and sized.  The last warp to finish
+// resets the counter for the next launch.  A wait that runs out sets *err (host-mapped); the warp
+// drains its copies and stops.
 constexpr uint64_t kBulkWaitNs = 2000000000ull;  // 2 s
 
 template <typename T, int CH, int S, int WARPS_>
@@ -170,13 +173,13 @@ struct LocalBulk {
 };
 
 // Every variant (k_local_vec and each staged configuration) gives lane (c, g) the pairs g, g + PW,
-// g + 2 PW, ... of its row in that order with the same per-pair arithmetic, so all produce the same
-// bits and the plan-time autotuner may pick any of them.
+// g + 2 PW, ... of its row in that order with the same per-pair arithmetic, and each row is summed
+// by one warp, so all produce the same bits and the plan-time autotuner may pick any of them.
 template <typename T, int CH, int S, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_local_bulk(int64_t Mt, const int64_t* __restrict__ rowptr,
                                                     const int* __restrict__ col, const T* __restrict__ eta,
                                                     const T* __restrict__ siglin, double* __restrict__ uloc,
-                                                    int* err) {
+                                                    int* err, int* sched) {
     using V = typename Vec16<T>::type;
     using G = LocalBulk<T, CH, S, WARPS>;
     constexpr int LP = 32 * sizeof(T) / 16;  // lanes per pair
@@ -184,70 +187,87 @@ __global__ void __launch_bounds__(WARPS * 32) k_local_bulk(int64_t Mt, const int
     static_assert(CH % 4 == 0 && CH % PW == 0, "stage must hold whole 4-slot groups");
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t row = (int64_t)blockIdx.x * G::WARPS + warp;
-    if (row >= Mt) return;
     unsigned char* base = smem + warp * G::WARPB;
     uint64_t* bar = (uint64_t*)(base + S * G::STAGE);
-    const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
-    const int nst = (int)((p1 - p0 + CH - 1) / CH);
     if (lane == 0) {
         for (int s = 0; s < S; s++) mbar_init(bar + s, 1);
         fence_mbar_init();
     }
     __syncwarp();
-    auto issue = [&](int k) {  // stage k of the row into buffer k % S (lane 0)
-        const int b = k % S;
-        const int64_t q0 = p0 + (int64_t)k * CH;
-        const uint32_t np = (uint32_t)min((int64_t)CH, p1 - q0);
-        unsigned char* dst = base + b * G::STAGE;
-        mbar_expect_tx(bar + b, np * G::ROWB + np * 4);
-        bulk_g2s(dst, eta + q0 * 32, np * G::ROWB, bar + b);
-        bulk_g2s(dst + CH * G::ROWB, col + q0, np * 4, bar + b);
-    };
-    if (lane == 0)
-        for (int k = 0; k < min(S, nst); k++) issue(k);
     const int c = lane % LP, g = lane / LP;
     const V* X = (const V*)siglin;
-    double d0 = 0.0, d1 = 0.0;  // FP64 path (as k_local_vec)
-    float sm = 0.f, cm = 0.f;                       // FP32 path: compensated sum
-    int k = 0;
-    for (; k < nst; k++) {
-        const int b = k % S;
-        const bool ok = mbar_wait_bounded(bar + b, (uint32_t)((k / S) & 1), kBulkWaitNs);
-        if (!__all_sync(0xffffffffu, ok)) break;
-        const int np = (int)min((int64_t)CH, p1 - p0 - (int64_t)k * CH);
-        const V* E = (const V*)(base + b * G::STAGE);
-        const int* C = (const int*)(base + b * G::STAGE + CH * G::ROWB);
+    uint32_t kk = 0;  // stages this warp has consumed: stage kk goes to buffer kk % S, phase (kk / S) & 1
+    for (;;) {
+        int row = 0;
+        if (lane == 0) row = atomicAdd(sched, 1);
+        row = __shfl_sync(0xffffffffu, row, 0);
+        if ((int64_t)row >= Mt) break;
+        const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
+        const int nst = (int)((p1 - p0 + CH - 1) / CH);
+        auto issue = [&](int k) {  // stage k of the row (lane 0)
+            const int b = (int)((kk + k) % S);
+            const int64_t q0 = p0 + (int64_t)k * CH;
+            const uint32_t np = (uint32_t)min((int64_t)CH, p1 - q0);
+            unsigned char* dst = base + b * G::STAGE;
+            mbar_expect_tx(bar + b, np * G::ROWB + np * 4);
+            bulk_g2s(dst, eta + q0 * 32, np * G::ROWB, bar + b);
+            bulk_g2s(dst + CH * G::ROWB, col + q0, np * 4, bar + b);
+        };
+        if (lane == 0)
+            for (int k = 0; k < min(S, nst); k++) issue(k);
+        double d0 = 0.0, d1 = 0.0;  // FP64 path (as k_local_vec)
+        float sm = 0.f, cm = 0.f;   // FP32 path: compensated sum
+        int k = 0;
+        for (; k < nst; k++) {
+            const uint32_t idx = kk + k;
+            const int b = (int)(idx % S);
+            const bool ok = mbar_wait_bounded(bar + b, (idx / S) & 1, kBulkWaitNs);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            const int np = (int)min((int64_t)CH, p1 - p0 - (int64_t)k * CH);
+            const V* E = (const V*)(base + b * G::STAGE);
+            const int* C = (const int*)(base + b * G::STAGE + CH * G::ROWB);
 #pragma unroll 4
-        for (int q = g; q < np; q += PW) {
-            const V e = E[q * LP + c];
-            const V x = __ldg(X + (int64_t)C[q] * LP + c);
-            if constexpr (sizeof(T) == 8) {
-                d0 = fma(e.x, x.x, d0);
-                d1 = fma(e.y, x.y, d1);
-            } else {
-                kahan_add(sm, cm, fmaf(e.w, x.w, fmaf(e.z, x.z, fmaf(e.y, x.y, e.x * x.x))));
+            for (int q = g; q < np; q += PW) {
+                const V e = E[q * LP + c];
+                const V x = __ldg(X + (int64_t)C[q] * LP + c);
+                if constexpr (sizeof(T) == 8) {
+                    d0 = fma(e.x, x.x, d0);
+                    d1 = fma(e.y, x.y, d1);
+                } else {
+                    kahan_add(sm, cm, fmaf(e.w, x.w, fmaf(e.z, x.z, fmaf(e.y, x.y, e.x * x.x))));
+                }
+            }
+            __syncwarp();
+            if (lane == 0 && k + S < nst) {
+                fence_proxy_async_smem();
+                issue(k + S);
             }
         }
-        __syncwarp();
-        if (lane == 0 && k + S < nst) {
-            fence_proxy_async_smem();
-            issue(k + S);
+        if (k < nst) {  // a wait ran out: record it, let the copies in flight land, leave the row unset
+            if (lane == 0) *(volatile int*)err = 1;
+            for (int j = k; j < min(nst, k + S); j++)
+                mbar_wait_bounded(bar + (kk + j) % S, ((kk + j) / S) & 1, kBulkWaitNs);
+            __syncwarp();
+            break;
+        }
+        kk += nst;
+        double tot;
+        if constexpr (sizeof(T) == 8)
+            tot = d0 + d1;
+        else
+            tot = (double)sm - (double)cm;
+        tot = warp_sum(tot);
+        if (lane == 0) uloc[row] = tot;
+    }
+    // every warp counts itself out; the last one resets the row counter for the next launch
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(sched + 1, 1) == (int)(gridDim.x * WARPS) - 1) {
+            sched[0] = 0;
+            sched[1] = 0;
+            __threadfence();
         }
     }
-    if (k < nst) {  // a wait ran out: record it, let the copies in flight land, leave the row unset
-        if (lane == 0) *(volatile int*)err = 1;
-        for (int j = k; j < min(nst, k + S); j++) mbar_wait_bounded(bar + j % S, (uint32_t)((j / S) & 1), kBulkWaitNs);
-        __syncwarp();
-        return;
-    }
-    double tot;
-    if constexpr (sizeof(T) == 8)
-        tot = d0 + d1;
-    else
-        tot = (double)sm - (double)cm;
-    tot = warp_sum(tot);
-    if (lane == 0) uloc[row] = tot;
 }
 
 static inline unsigned nblk_u(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -257,8 +277,18 @@ static inline unsigned nblk_u(int64_t n, int b) { return (unsigned)((n + b - 1) 
 template <typename T, int CH, int S, int WARPS>
 static void bulk_one(const Plan& pl, cudaStream_t st) {
     using G = LocalBulk<T, CH, S, WARPS>;
-    k_local_bulk<T, CH, S, WARPS><<<(unsigned)((pl.Mt + WARPS - 1) / WARPS), WARPS * 32, G::SMEM, st>>>(
-        pl.Mt, pl.d_rowptr, pl.d_col, (const T*)pl.d_eta, (const T*)pl.d_siglin, pl.d_uloc, pl.d_err);
+    // persistent grid: the CTAs that fit on the device at once (found once per kernel instance)
+    static int fit = 0;
+    if (fit == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_local_bulk<T, CH, S, WARPS>, WARPS * 32, G::SMEM);
+        fit = std::max(1, sms * std::max(per, 1));
+    }
+    const int64_t need = (pl.Mt + WARPS - 1) / WARPS;
+    k_local_bulk<T, CH, S, WARPS><<<(unsigned)std::min<int64_t>(need, fit), WARPS * 32, G::SMEM, st>>>(
+        pl.Mt, pl.d_rowptr, pl.d_col, (const T*)pl.d_eta, (const T*)pl.d_siglin, pl.d_uloc, pl.d_err, pl.d_sched);
 }
 template <typename T, int CH, int S, int WARPS>
 static void bulk_attr() {

@@ -701,6 +701,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(mem.alloc(&pl.d_uself, Mt));
         CK(mem.alloc(&pl.d_u_out, Mt));
     }
+    CK(mem.alloc(&pl.d_sched, 2));
     CK(cudaHostAlloc(&pl.h_err, sizeof(int), cudaHostAllocMapped));
     *(volatile int*)pl.h_err = 0;
     CK(cudaHostGetDevicePointer((void**)&pl.d_err, pl.h_err, 0));

@@ -134,6 +134,7 @@ struct Plan {
     // device-side error flag (a bounded wait that ran out), host-mapped pinned memory
     int* h_err = nullptr;
     int* d_err = nullptr;
+    int* d_sched = nullptr;      // row counter and finished-warp count of the persistent local kernel
 
     // host staging
     double* h_sig = nullptr;     // pinned
