@@ -57,7 +57,7 @@ __global__ void k_ingest(const int64_t* __restrict__ d_step, int64_t M, const do
 //   Z_l(t_{n+1}) = r_l Z_l(t_n) + r_l^W sigma_{n+1-W}.
 constexpr int kMaxWFar = 32;
 
-constexpr int kSelfGroups = 16;
+constexpr int kSelfGroups = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kSelfGroups) k_self(const int64_t* __restrict__ d_step, int64_t n_self,
@@ -80,10 +80,22 @@ __global__ void __launch_bounds__(32 * kSelfGroups) k_self(const int64_t* __rest
         const T* win = sigwin + (int64_t)self_src[s] * NW;
         for (int q = g; q < W - 1; q += G) u = fma(shead[q], (double)win[(n - 1 - q) & (NW - 1)], u);
         const double x = (double)win[(n + 1 - W) & (NW - 1)];
-        for (int l = g; l < nsoe; l += G) {
-            const double z = Y[(int64_t)l * n_self + s];
-            u = fma(sw[l], z, u);
-            Y[(int64_t)l * n_self + s] = fma(sdecay[l], z, sforce[l] * x);
+        // terms l = g, g + G, ... in batches of 8 with every load of a batch issued first
+        for (int l0 = g; l0 < nsoe; l0 += 8 * G) {
+            double z[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int l = l0 + k * G;
+                if (l < nsoe) z[k] = Y[(int64_t)l * n_self + s];
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int l = l0 + k * G;
+                if (l < nsoe) {
+                    u = fma(sw[l], z[k], u);
+                    Y[(int64_t)l * n_self + s] = fma(sdecay[l], z[k], sforce[l] * x);
+                }
+            }
         }
     }
     s_red[g][threadIdx.x] = u;
@@ -438,7 +450,7 @@ __global__ void __launch_bounds__(256) k_modes_pair(
 // alpha_F is added to the type-2 coefficient written by k_modes.  Block (32, G): 32 far modes x G
 // groups of terms; the W newest lagged levels of the block's modes are staged in shared memory.
 // H and Phi are stored [term][|k|], so the 32 modes of a warp (ordered by |k|) read neighbours.
-constexpr int kFarGroups = 16;
+constexpr int kFarGroups = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kFarGroups) k_far(
@@ -476,15 +488,30 @@ __global__ void __launch_bounds__(32 * kFarGroups) k_far(
         }
         const C st = s_S[W - 1][threadIdx.x];
         const double sx = st.x, sy = st.y;
-        for (int l = g; l < nlam; l += G) {
-            double2 b = B[(int64_t)l * n_far + f];
-            const double d = fdecay[l], fo = fforce[l];
-            b.x = fma(d, b.x, fo * sx);
-            b.y = fma(d, b.y, fo * sy);
-            B[(int64_t)l * n_far + f] = b;
-            const double hl = H[(int64_t)l * n_fk + fk];
-            aF.x = fma(hl, b.x, aF.x);
-            aF.y = fma(hl, b.y, aF.y);
+        // terms l = g, g + G, ... in batches of 8 with every load of a batch issued first
+        for (int l0 = g; l0 < nlam; l0 += 8 * G) {
+            double2 b[8];
+            double hl[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int l = l0 + u * G;
+                if (l < nlam) {
+                    b[u] = B[(int64_t)l * n_far + f];
+                    hl[u] = H[(int64_t)l * n_fk + fk];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int l = l0 + u * G;
+                if (l < nlam) {
+                    const double d = fdecay[l], fo = fforce[l];
+                    b[u].x = fma(d, b[u].x, fo * sx);
+                    b[u].y = fma(d, b[u].y, fo * sy);
+                    B[(int64_t)l * n_far + f] = b[u];
+                    aF.x = fma(hl[u], b[u].x, aF.x);
+                    aF.y = fma(hl[u], b[u].y, aF.y);
+                }
+            }
         }
     }
     s_red[g][threadIdx.x] = aF;
