@@ -26,6 +26,8 @@
  *   - After WFP_ECUDA a plan is poisoned: every later call except wfp_destroy returns
  *     WFP_ESTATE.
  *   - One plan must not be used from two threads at once; distinct plans are independent.
+ *   - A NULL stream means the calling thread's default stream (the library is built with
+ *     per-thread default streams), so plans created on different threads do not serialise.
  *   - wfp_last_error() returns a thread-local message describing the last failure.
  */
 #ifndef WFP_H
@@ -265,7 +267,9 @@ wfp_status wfp_local_noalloc(int64_t M, const double* src_xy, int64_t Mt, const 
  *      free part of hbm_budget_bytes (a request that does not fit waits; later, smaller ones may
  *      pass it); a request is admitted with its S history stored (WFP_LAG_STORE) when that
  *      footprint fits, else with the lagged NUFFT (WFP_LAG_RECOMPUTE); at most max_active
- *      requests are active at once; a request larger than the whole budget fails;
+ *      requests are admitted at once; a request larger than the whole budget fails.  An admitted
+ *      request's plan is built on a worker thread (WFP_REQ_BUILDING) while the active requests
+ *      keep stepping; it joins the active set on the first tick after its build completes;
  *   2. enqueues one step of every active request, each on its own stream, so that kernels of
  *      different requests overlap on the device; the host runs at most two steps ahead of the
  *      device per request (before enqueueing step n it waits for step n - 2);
@@ -300,7 +304,7 @@ typedef struct {
     const int64_t* out_steps;     /* host, n_out step indices in 1..N_t (any order; kept sorted) */
 } wfp_request;
 
-enum { WFP_REQ_PENDING = 0, WFP_REQ_ACTIVE = 1, WFP_REQ_DONE = 2, WFP_REQ_FAILED = 3 };
+enum { WFP_REQ_PENDING = 0, WFP_REQ_ACTIVE = 1, WFP_REQ_DONE = 2, WFP_REQ_FAILED = 3, WFP_REQ_BUILDING = 4 };
 
 typedef struct {
     int state;                    /* WFP_REQ_* */

@@ -20,7 +20,10 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libwfp.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# per-thread default streams: work a thread issues without a stream (plan building) does not
+# serialise with other threads' streams, so the request server can build plans while others step
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+           "--default-stream", "per-thread",
            "-I", INC, "-I", CSRC]
 
 

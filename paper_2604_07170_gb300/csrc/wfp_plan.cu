@@ -357,7 +357,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
                                                      eta);
             CK(cudaGetLastError());
         }
-        CK(cudaDeviceSynchronize());
+        CK(cudaStreamSynchronize(cudaStreamPerThread));
     }
 
     // ---- near-history modes: half-plane disk |n| dk <= Km (n2 > 0, or n2 = 0 and n1 >= 0)
@@ -430,7 +430,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         k_taps<T><<<nblk(pl.n_kappa, 128), 128>>>(pl.n_kappa, d_kap.p, P.dt, P.W, P.Aplus - P.delta, ngt, d_sq.p,
                                                   d_wq.p, d_f1.p, d_f2.p, taps, pl.d_rot);
         CK(cudaGetLastError());
-        CK(cudaDeviceSynchronize());
+        CK(cudaStreamSynchronize(cudaStreamPerThread));
     }
 
     // ---- far history (Sec. 5): far modes |k| <= Kf, SOE (Sec. 2.3), Hankel coefficients, taps
@@ -507,7 +507,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(upload(mem, &pl.d_fdecay, fdec));
         CK(upload(mem, &pl.d_fforce, ffor));
         CK(mem.alloc(&pl.d_B, (size_t)P.n_lambda * pl.n_far));
-        CK(cudaDeviceSynchronize());
+        CK(cudaStreamSynchronize(cudaStreamPerThread));
     }
 
     // ---- self term of coincident pairs: SOE of 1/d on [d_lo, T] with phi(d_lo) <= eps/100
@@ -710,7 +710,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
     CK(cudaMallocHost(&pl.h_sig, std::max<int64_t>(M, 1) * sizeof(double)));
     CK(cudaMallocHost(&pl.h_u, std::max<int64_t>(Mt, 1) * sizeof(double)));
     CK(cudaEventCreateWithFlags(&pl.ev_out, cudaEventDisableTiming));
-    CK(cudaDeviceSynchronize());
+    CK(cudaStreamSynchronize(cudaStreamPerThread));
 
     // ---- spreading autotuner: every candidate tiling gives the same bits (ascending source order
     // per grid point), so the fastest on this device and workload is kept
@@ -766,7 +766,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(upload(mem, &pl.d_tile_xy, tl.txy));
         CK(upload(mem, &pl.d_tile_ptr, tl.tptr));
         CK(upload(mem, &pl.d_tile_src, tl.tsrc));
-        CK(cudaDeviceSynchronize());
+        CK(cudaStreamSynchronize(cudaStreamPerThread));
     }
 
     // ---- local-part autotuner: all variants give the same bits; keep the fastest

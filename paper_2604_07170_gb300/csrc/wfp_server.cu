@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -21,6 +22,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "wfp.h"
@@ -79,6 +81,11 @@ struct Request {
     double t_submit = 0, t_admit = 0, t_done = 0;
     std::string err;
     cudaEvent_t ev[2] = {nullptr, nullptr};  // completion of the last two enqueued steps
+    // plan building on a worker thread (the builder writes plan, buffers, build_status and err,
+    // then sets build_done; the server thread reads them only after seeing build_done)
+    std::thread builder;
+    std::atomic<int> build_done{0};
+    wfp_status build_status = WFP_OK;
 };
 
 // Device bytes a plan for this request would hold (the allocations of the plan builder, the
@@ -170,7 +177,9 @@ struct wfp_server_s {
     int64_t next_id = 1;
     int64_t n_admitted = 0;  // requests admitted so far
     std::deque<Request*> pending;
+    std::vector<Request*> building;  // admitted, plan being built on a worker thread
     std::vector<Request*> active;
+    int max_builders = 1;
     std::map<int64_t, std::unique_ptr<Request>> all;
     int device = 0;
 };
@@ -198,8 +207,7 @@ static void retire(wfp_server_s* sv, Request* r, int state) {
 }
 
 // build the plan and device buffers of an admitted request
-static wfp_status admit(wfp_server_s* sv, Request* r, bool store, std::string& err) {
-    wfp_opts o = sv->opts;
+static wfp_status admit_with(wfp_opts o, Request* r, bool store, std::string& err) {
     o.lag_mode = store ? WFP_LAG_STORE : WFP_LAG_RECOMPUTE;
     o.stream = nullptr;  // every request gets its own stream
     wfp_status st = wfp_plan_create(r->M, r->src.data(), r->Mt, r->tgt.data(), r->dt, r->Nt, r->K0, r->tol, &o,
@@ -224,9 +232,19 @@ static wfp_status admit(wfp_server_s* sv, Request* r, bool store, std::string& e
         err = "request parameters: copy failed";
         return WFP_ECUDA;
     }
-    r->state = WFP_REQ_ACTIVE;
-    r->t_admit = now_s();
     return WFP_OK;
+}
+
+// worker thread: build the request's plan and buffers (per-thread default stream, so the steps
+// of the active requests keep running)
+static void build_worker(int device, const wfp_opts* opts, Request* r, bool store) {
+    cudaSetDevice(device);
+    std::string err;
+    wfp_opts o = *opts;
+    r->build_status = admit_with(o, r, store, err);
+    if (r->build_status != WFP_OK) r->err = err;
+    cudaStreamSynchronize(cudaStreamPerThread);
+    r->build_done.store(1, std::memory_order_release);
 }
 
 extern "C" {
@@ -290,8 +308,11 @@ wfp_status wfp_server_tick(wfp_server sv, int* n_active, int* n_pending) {
         r->state = WFP_REQ_FAILED;
         r->t_done = now_s();
     };
-    // (1) admission: arrival order, first fit within the HBM budget and the slot limit
-    for (auto it = sv->pending.begin(); it != sv->pending.end() && (int)sv->active.size() < sv->max_active;) {
+    // (1) admission: arrival order, first fit within the HBM budget and the slot limit; the plan is
+    // built on a worker thread while the active requests keep stepping
+    for (auto it = sv->pending.begin(); it != sv->pending.end() &&
+                                        (int)(sv->active.size() + sv->building.size()) < sv->max_active &&
+                                        (int)sv->building.size() < sv->max_builders;) {
         Request* r = *it;
         std::string err;
         int64_t est[2];
@@ -312,20 +333,36 @@ wfp_status wfp_server_tick(wfp_server sv, int* n_active, int* n_pending) {
             ++it;
             continue;
         }
-        if (admit(sv, r, store, err) != WFP_OK) {
+        r->bytes = need;  // reserved until the request retires or its build fails
+        sv->used += need;
+        sv->n_admitted++;
+        r->state = WFP_REQ_BUILDING;
+        r->t_admit = now_s();
+        r->builder = std::thread(build_worker, sv->device, &sv->opts, r, store);
+        sv->building.push_back(r);
+        it = sv->pending.erase(it);
+    }
+    // finished builds become active (or fail and give their reservation back)
+    for (size_t i = 0; i < sv->building.size();) {
+        Request* r = sv->building[i];
+        if (!r->build_done.load(std::memory_order_acquire)) {
+            i++;
+            continue;
+        }
+        r->builder.join();
+        sv->building.erase(sv->building.begin() + i);
+        if (r->build_status != WFP_OK) {
             release(r);
-            fail_pending(r, err);
-            it = sv->pending.erase(it);
+            sv->used -= r->bytes;
+            r->state = WFP_REQ_FAILED;
+            r->t_done = now_s();
             continue;
         }
         wfp_info info;
         wfp_plan_get_info(r->plan, &info);
         r->plan_bytes = info.device_bytes;
-        r->bytes = need;
-        sv->used += need;
-        sv->n_admitted++;
+        r->state = WFP_REQ_ACTIVE;
         sv->active.push_back(r);
-        it = sv->pending.erase(it);
     }
     // (2) enqueue one step of every active request on its own stream.  At most two steps of a
     // request are in flight: before enqueueing step n the host waits for step n - 2.
@@ -380,7 +417,7 @@ wfp_status wfp_server_tick(wfp_server sv, int* n_active, int* n_pending) {
         }
         i++;
     }
-    if (n_active) *n_active = (int)sv->active.size();
+    if (n_active) *n_active = (int)(sv->active.size() + sv->building.size());
     if (n_pending) *n_pending = (int)sv->pending.size();
     return WFP_OK;
 }
@@ -390,12 +427,13 @@ wfp_status wfp_server_run(wfp_server sv) {
     int a = 1, p = 1;
     while (a > 0 || p > 0) {
         const int64_t before = sv->n_admitted;
-        const bool idle = sv->active.empty();
+        const bool idle = sv->active.empty() && sv->building.empty();
         wfp_status st = wfp_server_tick(sv, &a, &p);
         if (st != WFP_OK) return st;
-        // a round that began with nothing active admitted nothing: the pending requests never fit
+        // a round that began with nothing admitted admitted nothing: the pending requests never fit
         if (idle && a == 0 && p > 0 && sv->n_admitted == before)
             return sfail(WFP_ENOMEM, "pending requests cannot be admitted");
+        if (sv->active.empty() && !sv->building.empty()) std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
     return WFP_OK;
 }
@@ -431,6 +469,11 @@ wfp_status wfp_server_result(wfp_server sv, int64_t id, double* u_out) {
 
 wfp_status wfp_server_destroy(wfp_server sv) {
     if (!sv) return WFP_OK;
+    for (Request* r : sv->building) {  // let running builds finish, then drop them
+        r->builder.join();
+        r->err = "abandoned: server destroyed";
+        retire(sv, r, WFP_REQ_FAILED);
+    }
     for (Request* r : sv->active) {
         r->err = "abandoned: server destroyed";
         retire(sv, r, WFP_REQ_FAILED);

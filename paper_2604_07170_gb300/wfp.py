@@ -59,7 +59,7 @@ EXPORTS = ["wfp_opts_default", "wfp_plan_create", "wfp_step", "wfp_destroy", "wf
            "wfp_server_run", "wfp_server_query", "wfp_server_result", "wfp_server_destroy"]
 
 SIGNAL_GAUSS3, SIGNAL_ERF = 0, 1
-REQ_PENDING, REQ_ACTIVE, REQ_DONE, REQ_FAILED = range(4)
+REQ_PENDING, REQ_ACTIVE, REQ_DONE, REQ_FAILED, REQ_BUILDING = range(5)
 
 
 class wfp_request(ctypes.Structure):

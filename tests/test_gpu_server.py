@@ -60,6 +60,9 @@ def test_admission_respects_the_budget_and_arrival_order():
     with wfp.Server(64 << 30, 16) as probe:  # learn one request's footprint
         i0 = _submit(probe, wls[0])
         probe.tick()
+        assert probe.query(i0)["state"] in (wfp.REQ_BUILDING, wfp.REQ_ACTIVE)
+        while probe.query(i0)["state"] == wfp.REQ_BUILDING:  # the plan is built on a worker thread
+            probe.tick()
         need = probe.query(i0)["device_bytes"]
         plan_bytes = probe.query(i0)["plan_bytes"]
     # the admission estimate covers what the plan really holds (plus the cuFFT work areas)
