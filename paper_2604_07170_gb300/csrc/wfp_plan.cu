@@ -111,9 +111,15 @@ __global__ void __launch_bounds__(128) k_eta(int64_t npairs, const double* __res
 template <typename TT>
 __global__ void k_taps(int64_t nk, const double* __restrict__ kap, double dt, int W, double lagshift, int ngt,
                        const double* __restrict__ sq, const double* __restrict__ wq, const double* __restrict__ f1,
-                       const double* __restrict__ f2, TT* __restrict__ taps, double* __restrict__ rot) {
+                       const double* __restrict__ f2, TT* __restrict__ taps, double* __restrict__ rot, bool compact) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nk) return;
+    if constexpr (sizeof(TT) == 4) {
+        if (compact) {  // lag never active: p and q only
+            mode_taps(kap[i], dt, W, lagshift, ngt, sq, wq, f1, f2, TapsCompact{taps + i * 4 * W}, rot + 3 * i);
+            return;
+        }
+    }
     const int per = (sizeof(TT) == 8) ? 4 : 8;
     mode_taps(kap[i], dt, W, lagshift, ngt, sq, wq, f1, f2, TapsInterleaved<TT>{taps + i * per * W}, rot + 3 * i);
 }
@@ -424,11 +430,12 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(upload_tmp(d_f1, f1));
         CK(upload_tmp(d_f2, f2));
         T* taps = nullptr;
-        CK(mem.alloc(&taps, (size_t)pl.n_kappa * (sizeof(T) == 8 ? 4 : 8) * P.W));
+        pl.compact_taps = (sizeof(T) == 4) && !P.lag_active;
+        CK(mem.alloc(&taps, (size_t)pl.n_kappa * (sizeof(T) == 8 || pl.compact_taps ? 4 : 8) * P.W));
         pl.d_taps = taps;
         CK(mem.alloc(&pl.d_rot, (size_t)pl.n_kappa * 3));
         k_taps<T><<<nblk(pl.n_kappa, 128), 128>>>(pl.n_kappa, d_kap.p, P.dt, P.W, P.Aplus - P.delta, ngt, d_sq.p,
-                                                  d_wq.p, d_f1.p, d_f2.p, taps, pl.d_rot);
+                                                  d_wq.p, d_f1.p, d_f2.p, taps, pl.d_rot, pl.compact_taps);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(cudaStreamPerThread));
     }
@@ -588,6 +595,8 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         std::vector<double> fac(P.Nh + 1);
         for (int n = 0; n <= P.Nh; n++) fac[n] = ((n & 1) ? -1.0 : 1.0) * P.h / psihat[n];
         CK(upload(mem, &pl.d_fac, fac));
+        std::vector<float> facf(fac.begin(), fac.end());
+        CK(upload(mem, &pl.d_facf, facf));
         // tiles of the band touched by each source footprint, for each candidate tile side; the
         // autotuner below times them and keeps one
         const int opt_ts = pl.opts.spread_tile, opt_ch = pl.opts.spread_chunk;

@@ -88,6 +88,7 @@ struct Plan {
     void* d_te = nullptr;        // [nf][nf/2+1] complex
     void* d_tf = nullptr;        // [nb][nf] real: type-2 grid in the band
     double* d_fac = nullptr;     // [Nh+1] (-1)^n h / psihat(n)
+    float* d_facf = nullptr;     // the same in FP32 (mixed-path deconvolution)
     cufftHandle fftA = 0, fftB = 0, fftBi = 0, fftAi = 0;
     bool fft_made[4] = {false, false, false, false};
 
@@ -95,6 +96,7 @@ struct Plan {
     int64_t n_modes = 0, n_kappa = 0;
     int2* d_mode_n = nullptr;    // (n1, n2)
     int* d_mode_k = nullptr;     // distinct-|k| index
+    bool compact_taps = false;   // mixed path without lag: taps hold p and q only (4 floats per level)
     void* d_taps = nullptr;      // [n_kappa][4W] p, q, pA, qA (Eq. hggrid), step dt folded in
     double* d_rot = nullptr;     // [n_kappa][3] cos(k dt), sin(k dt)/k, k sin(k dt)
     double2* d_alpha = nullptr;  // [n_modes]

@@ -164,6 +164,20 @@ struct TapsInterleaved<float> {
     }
 };
 
+// FP32 hi/lo pairs of p and q only (plans whose lag never activates): per level {p hi, p lo},
+// {q hi, q lo} -- one float2 per FIR
+struct TapsCompact {
+    float* t;
+    WFP_HD void operator()(int m, double p, double q, double, double) const {
+        const double v[2] = {p, q};
+        for (int i = 0; i < 2; i++) {
+            const float hi = (float)v[i];
+            t[4 * m + 2 * i] = hi;
+            t[4 * m + 2 * i + 1] = (float)(v[i] - (double)hi);
+        }
+    }
+};
+
 template <typename Put>
 WFP_HD inline void mode_taps(double kappa, double dt, int W, double lagshift, int ngt, const double* sq,
                              const double* wq, const double* f1, const double* f2, const Put& put, double* rot) {

@@ -325,9 +325,10 @@ __global__ void __launch_bounds__(256) k_modes(
 // and nothing persists in alpha.  The newest current and lagged levels come from registers.
 // Thread 0 advances alpha with h and writes the type-2 coefficient, thread 1 advances alpha-dot
 // with g (Eq. alphakEvolution, FP64).
+template <bool COMPACT>
 __global__ void __launch_bounds__(256) k_modes_pair(
     const int64_t* __restrict__ d_step, int64_t n_modes, int W, int L, int Nh, int nf, const int2* __restrict__ mode_n,
-    const int* __restrict__ mode_k, const double* __restrict__ fac, double coef2, const float2* __restrict__ tc_cur,
+    const int* __restrict__ mode_k, const float* __restrict__ facf, float coef2, const float2* __restrict__ tc_cur,
     const float2* __restrict__ tc_lag, float2* __restrict__ ring, float2* __restrict__ ring_lag, int R_cur, int R_lag,
     int lag_off, int write_lag, const float* __restrict__ taps, const double* __restrict__ rot,
     double2* __restrict__ alpha, double2* __restrict__ alphad, float2* __restrict__ td, int64_t near_sq) {
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(256) k_modes_pair(
     int2 nn = make_int2(0, 0);
     int kid = 0;
     int64_t gi = 0;
-    double f = 0.0;
+    float f = 0.f;
     float2 s_cur = make_float2(0.f, 0.f), s_lag = make_float2(0.f, 0.f);
     const int slot = (int)(n % R_cur);
     const int slot_lag = (int)((((n - L + lag_off) % R_lag) + R_lag) % R_lag);  // level n - L
@@ -349,16 +350,16 @@ __global__ void __launch_bounds__(256) k_modes_pair(
         kid = mode_k[m];
         const int row = nn.x < 0 ? nn.x + nf : nn.x;
         gi = (int64_t)row * (Nh + 1) + nn.y;
-        f = fac[nn.x < 0 ? -nn.x : nn.x] * fac[nn.y];
+        f = facf[nn.x < 0 ? -nn.x : nn.x] * facf[nn.y];  // deconvolution, FP32 like the transform
         const float2 t = tc_cur[gi];
-        s_cur.x = (float)((double)t.x * f);
-        s_cur.y = (float)(-(double)t.y * f);
+        s_cur.x = t.x * f;
+        s_cur.y = -t.y * f;
         if (r == 0) ring[(int64_t)slot * n_modes + m] = s_cur;
         if (lag) {
             if (write_lag) {  // lagged NUFFT result: level n - L
                 const float2 u = tc_lag[gi];
-                s_lag.x = (float)((double)u.x * f);
-                s_lag.y = (float)(-(double)u.y * f);
+                s_lag.x = u.x * f;
+                s_lag.y = -u.y * f;
                 if (r == 1) ring_lag[(int64_t)slot_lag * n_modes + m] = s_lag;
             } else {
                 s_lag = ring_lag[(int64_t)slot_lag * n_modes + m];
@@ -369,8 +370,11 @@ __global__ void __launch_bounds__(256) k_modes_pair(
     const bool near = valid && (int64_t)nn.x * nn.x + (int64_t)nn.y * nn.y <= near_sq;
     float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f;
     if (near) {
-        const float4* tp = (const float4*)(taps + (int64_t)kid * 8 * W) + r;  // this thread's FIR
-        constexpr int U = 4;
+        // this thread's FIR taps per level: {tap, tapA} hi and lo (float4), or {tap hi, tap lo}
+        // (float2) when the plan's lag never activates
+        const float4* tp4 = (const float4*)(taps + (int64_t)kid * 8 * W) + r;
+        const float2* tp2 = (const float2*)(taps + (int64_t)kid * 4 * W) + r;
+        constexpr int U = 4;  // levels whose loads are in flight together
         int sl = slot, sll = slot_lag;
         for (int j0 = 0; j0 < W; j0 += U) {
             float2 a[U], b[U];
@@ -379,14 +383,19 @@ __global__ void __launch_bounds__(256) k_modes_pair(
             for (int u = 0; u < U; u++) {
                 const int j = j0 + u;
                 if (j < W) {
-                    t4[u] = tp[2 * j];
+                    if constexpr (COMPACT) {
+                        const float2 t2 = tp2[2 * j];
+                        t4[u] = make_float4(t2.x, 0.f, t2.y, 0.f);
+                    } else {
+                        t4[u] = tp4[2 * j];
+                    }
                     if (j == 0) {
                         a[u] = s_cur;
                         b[u] = s_lag;
                     } else {
                         const int s1 = sl - u < 0 ? sl - u + R_cur : sl - u;
                         a[u] = ring[(int64_t)s1 * n_modes + m];
-                        if (lag) {
+                        if (!COMPACT && lag) {
                             const int s2 = sll - u < 0 ? sll - u + R_lag : sll - u;
                             b[u] = ring_lag[(int64_t)s2 * n_modes + m];
                         }
@@ -398,7 +407,7 @@ __global__ void __launch_bounds__(256) k_modes_pair(
                 if (j0 + u < W) {
                     df_acc(xh, xl, t4[u].x, t4[u].z, a[u].x);
                     df_acc(yh, yl, t4[u].x, t4[u].z, a[u].y);
-                    if (lag) {
+                    if (!COMPACT && lag) {
                         df_acc(xh, xl, -t4[u].y, -t4[u].w, b[u].x);
                         df_acc(yh, yl, -t4[u].y, -t4[u].w, b[u].y);
                     }
@@ -425,13 +434,13 @@ __global__ void __launch_bounds__(256) k_modes_pair(
         an.x = fma(c, a.x, fma(sk, ad.x, vx));
         an.y = fma(c, a.y, fma(sk, ad.y, vy));
         alpha[m] = an;
-        const double cf = coef2 * f;
+        const float cf = coef2 * f;  // type-2 coefficient in the grid precision
         float2 o;
-        o.x = (float)(an.x * cf);
-        o.y = (float)(-an.y * cf);
+        o.x = (float)an.x * cf;
+        o.y = -(float)an.y * cf;
         td[gi] = o;
         if (nn.y == 0 && nn.x > 0) {
-            o.y = (float)(an.y * cf);
+            o.y = (float)an.y * cf;
             td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
         }
     } else {  // alphadot(t + dt) = -k sin(k dt) alpha + cos(k dt) alphadot + g
@@ -710,8 +719,9 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err) {
             pl.lag_off, pl.lag_store ? 0 : 1, (const T*)pl.d_taps, pl.d_rot, pl.d_alpha, pl.d_alphad, (C*)pl.d_td,
             near_sq);
     } else {
-        k_modes_pair<<<nblk(2 * pl.n_modes, 256), 256, 0, st>>>(
-            pl.d_step, pl.n_modes, P.W, P.L, P.Nh, P.nf, pl.d_mode_n, pl.d_mode_k, pl.d_fac, coef2,
+        auto kern = pl.compact_taps ? k_modes_pair<true> : k_modes_pair<false>;
+        kern<<<nblk(2 * pl.n_modes, 256), 256, 0, st>>>(
+            pl.d_step, pl.n_modes, P.W, P.L, P.Nh, P.nf, pl.d_mode_n, pl.d_mode_k, pl.d_facf, (float)coef2,
             (const float2*)pl.d_tc_cur, (const float2*)pl.d_tc_lag, (float2*)pl.d_ring, (float2*)pl.d_ring_lag,
             pl.R_cur, pl.R_lag, pl.lag_off, pl.lag_store ? 0 : 1, (const float*)pl.d_taps, pl.d_rot, pl.d_alpha,
             pl.d_alphad, (float2*)pl.d_td, near_sq);
