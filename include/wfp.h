@@ -57,9 +57,13 @@ enum { WFP_FP64 = 0, WFP_MIXED = 1 };
  *                 FIR taps and local weights in FP32; mode state, its per-step rotation, the
  *                 sum-of-exponentials recurrences and all accumulations across sources in FP64.
  *   eps           internal tolerance epsilon; 0 => tol/1000.  b = ln(1/eps) (Sec. 2.1).
- *   W             blending width in steps, delta = W dt (Eq. W); 0 => ceil(2b/(pi - K0 dt)) (Eq. dt).
+ *   W             blending width in steps, delta = W dt (Eq. W); 0 => ceil(delta / dt) when delta > 0,
+ *                 else ceil(2b/(pi - K0 dt)) (Eq. dt).  2 <= W <= 59 and Eq. dt must hold.
  *   p             interpolation order of the local part (Sec. 6); 0 => 20, lowered (even, >= 8) so
- *                 that nmax = W + 1 + p/2 <= 32.
+ *                 that nmax = W + 1 + p/2 fits a 32-level window, or else a 64-level one.
+ *   delta         fixed blending width in the caller's time units (the fixed-delta variant of the
+ *                 paper's remark on small time steps: delta stays put as dt shrinks and W grows);
+ *                 0 => derived from W as above.
  *   Kf            far-history cut-off wavenumber in normalised units (Sec. 5); 0 => derived from eps.
  *   upsampfac     minimum NUFFT fine-grid upsampling factor; 0 => 1.25 on the FP64 path; on the MIXED path
  *                 2.0 while that keeps the grid at most 4096 points a side, else 1.25.  The grid
@@ -106,6 +110,7 @@ typedef struct {
     int spread_chunk;
     int local_variant;
     int local_interp;
+    double delta;
 } wfp_opts;
 
 enum { WFP_INTERP_HYBRID = 0, WFP_INTERP_LAGRANGE = 1 };

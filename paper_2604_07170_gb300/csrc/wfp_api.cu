@@ -373,7 +373,7 @@ wfp_status wfp_profile_read(wfp_plan plan, int max_parts, const char** names, do
 
 // ------------------------------------------------------------------ host-only diagnostics
 wfp_status wfp_debug_eta(double r, double dt, int W, int p, double eps, double band_limit, int ng, double* eta) {
-    if (!eta || W < 2 || W > 32 || p < 2 || p > kMaxP || (p & 1) || ng < 2 || ng > 64)
+    if (!eta || W < 2 || W > 59 || p < 2 || p > kMaxP || (p & 1) || ng < 2 || ng > 64)
         return fail(WFP_EINVAL, "bad argument");
     int nmax = W + 1 + p / 2;
     if (nmax > kMaxLevels) return fail(WFP_EINVAL, "W + 1 + p/2 too large");
@@ -390,7 +390,7 @@ wfp_status wfp_debug_eta(double r, double dt, int W, int p, double eps, double b
 }
 
 wfp_status wfp_debug_taps(double kappa, double dt, int W, double eps, double lagshift, double* taps, double* rot) {
-    if (!taps || !rot || W < 2 || W > 32) return fail(WFP_EINVAL, "bad argument");
+    if (!taps || !rot || W < 2 || W > 59) return fail(WFP_EINVAL, "bad argument");
     double b = std::log(1.0 / eps), delta = W * dt;
     const int ngt = 24;
     std::vector<double> gx(ngt), gw(ngt), sq(ngt), wq(ngt), f1((size_t)W * ngt), f2((size_t)W * ngt);

@@ -324,19 +324,28 @@ wfp_status local_params(double dt, double K0, double tol, const wfp_opts& o, dou
         *why = "band_limit * dt must be below pi (Eq. dt)";
         return WFP_EINVAL;
     }
-    // Eq. dt: dt <= (pi - 2b/W)/K0  <=>  W >= 2b / (pi - K0 dt)
-    int w = (o.W > 0) ? o.W : (int)std::ceil(2.0 * b / (kPi - K0dt) - 1e-12);
+    // Eq. dt: dt <= (pi - 2b/W)/K0  <=>  W >= 2b / (pi - K0 dt).  A fixed blending width delta
+    // (the fixed-delta variant of the paper's remark on small time steps) sets W = ceil(delta / dt).
+    if (!(o.delta >= 0) || !std::isfinite(o.delta)) {
+        *why = "delta must be >= 0 and finite";
+        return WFP_EINVAL;
+    }
+    int w = (o.W > 0) ? o.W
+                      : (o.delta > 0 ? (int)std::ceil(o.delta / dt - 1e-9)
+                                     : (int)std::ceil(2.0 * b / (kPi - K0dt) - 1e-12));
     if (w < 2) w = 2;
     if (2.0 * b / w >= kPi - K0dt) {
         *why = "W too small for band_limit * dt (Eq. dt)";
         return WFP_EINVAL;
     }
-    if (w > 32) {
-        *why = "W must be <= 32 (dt too coarse for the band limit)";
+    if (w > 59) {
+        *why = "W must be <= 59 (dt too coarse for the band limit, or delta / dt too large)";
         return WFP_EINVAL;
     }
-    // default order 20 (Sec. 7), reduced if needed so that nmax = W + 1 + p/2 fits a 32-level window
-    int pp = (o.p > 0) ? o.p : std::max(8, std::min(20, 2 * (31 - w)));
+    // default order 20 (Sec. 7), reduced if needed so that nmax = W + 1 + p/2 fits a 32-level window,
+    // else a 64-level one
+    const int cap = (2 * (31 - w) >= 8) ? 31 : 63;
+    int pp = (o.p > 0) ? o.p : std::max(8, std::min(20, 2 * (cap - w)));
     if (pp % 2) pp += 1;
     if (pp > 32) {
         *why = "interpolation order p must be <= 32";

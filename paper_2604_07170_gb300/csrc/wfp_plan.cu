@@ -844,8 +844,8 @@ wfp_status plan_build(Plan& pl, const double* src_xy, const double* tgt_xy, std:
     P.Mt = Mt;
     P.cx = 0.5 * (xmin + xmax);
     P.cy = 0.5 * (ymin + ymax);
-    if (P.W > 32) {
-        err = "W > 32 is not supported";
+    if (P.W > 59) {
+        err = "W > 59 is not supported";
         return WFP_EUNSUPPORTED;
     }
     std::vector<double> sxy(2 * M), txy(2 * Mt);

@@ -55,7 +55,7 @@ __global__ void k_ingest(const int64_t* __restrict__ d_step, int64_t M, const do
 // [d_lo, T] and the trapezoid rule on the grid, arranged as a shared window plus one-tap recurrences:
 //   u_self(t_n) = sum_{q<W-1} g_q sigma_{n-1-q} + sum_l w'_l Z_l(t_n),
 //   Z_l(t_{n+1}) = r_l Z_l(t_n) + r_l^W sigma_{n+1-W}.
-constexpr int kMaxWFar = 32;
+constexpr int kMaxWFar = 64;  // W <= 59
 
 constexpr int kSelfGroups = 8;
 

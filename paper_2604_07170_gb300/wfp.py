@@ -28,7 +28,8 @@ class wfp_opts(ctypes.Structure):
                 ("Kf", _c_dbl), ("upsampfac", _c_dbl), ("kernel_width", ctypes.c_int),
                 ("soe_nodes", ctypes.c_int), ("exclude_self", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("use_graph", ctypes.c_int), ("lag_mode", ctypes.c_int), ("spread_tile", ctypes.c_int),
-                ("spread_chunk", ctypes.c_int), ("local_variant", ctypes.c_int), ("local_interp", ctypes.c_int)]
+                ("spread_chunk", ctypes.c_int), ("local_variant", ctypes.c_int), ("local_interp", ctypes.c_int),
+                ("delta", _c_dbl)]
 
 
 class wfp_info(ctypes.Structure):

@@ -61,3 +61,32 @@ def test_local_interpolation_order_convergence():
     assert errs[4] > errs[6] > errs[8]
     assert errs[4] > 100 * errs[10]
     assert errs[12] < 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fixed_delta_variant_with_a_64_level_window(precision):
+    # fixed blending width delta = 1.2 at dt = 0.025 (40 steps per period): W = 48 and nmax = 59, so
+    # the local part runs on the 64-level window; the default plan (W from Eq. dt) is checked too
+    from paper_2604_07170_gb300 import wfp
+    wl = inputs.small(100, 3.0, 400, seed=41, dt=0.025)
+    steps = [120, 250, 400]
+    ev = np.array([[x, y, n * wl.dt] for n in steps for (x, y) in wl.src_xy])
+    ref = oracle.field(wl.src_xy, wl.params, ev, r_coinc=1e-12 * wl.meta["box"]).reshape(len(steps), -1)
+    sig = wl.sigma(1, wl.n_steps + 1)
+    for kw in ({"delta": 1.2}, {}):
+        plan = wfp.Plan(wl.src_xy, None, wl.dt, wl.n_steps, wl.band_limit, wl.tol, precision=precision, **kw)
+        info = plan.info()
+        got = []
+        for n in range(1, wl.n_steps + 1):
+            u = plan.step(sig[n - 1])
+            if n in steps:
+                got.append(u)
+        plan.close()
+        got = np.array(got)
+        floor = 1e-2 * np.linalg.norm(ref, axis=1).max()
+        e = np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), floor)
+        print(f"\n{kw} W={info['W']} nmax={info['nmax']} local_variant={info['local_variant']} rel L2:", e)
+        if kw:
+            assert info["W"] == 48 and info["nmax"] > 32 and info["local_variant"] == 0
+        assert info["lag_active"] and info["far_active"]
+        assert e.max() <= (1e-6 if precision == 0 else 2e-6)
