@@ -226,3 +226,39 @@ def test_checkpoint_resume_gives_the_same_bits(precision, lag_mode):
     assert ei.value.code == wfp.WFP_EINVAL
     c.step(sig[0])
     c.close()
+
+
+def test_one_step_plan_and_zero_signals():
+    from paper_2604_07170_gb300 import wfp
+    # N_t = 1: the only step has no advance phase (signals start smoothly, so the field is ~0)
+    wl = inputs.small(50, 2.5, 1, seed=22)
+    plan = wfp.Plan(wl.src_xy, None, wl.dt, 1, wl.band_limit, wl.tol)
+    u = plan.step(wl.sigma(1, 2)[0])
+    with pytest.raises(wfp.WFPError) as ei:
+        plan.step(wl.sigma(1, 2)[0])
+    assert ei.value.code == wfp.WFP_ESTATE
+    plan.close()
+    ev = np.column_stack([wl.src_xy, np.full(wl.M, wl.dt)])
+    ref = oracle.field(wl.src_xy, wl.params, ev, r_coinc=1e-12 * wl.meta["box"])
+    assert np.all(np.isfinite(u)) and np.max(np.abs(u - ref)) <= 1e-12
+    # identically zero signals through every part (lag and far history active): exactly zero field
+    wl = inputs.small(60, 3.0, 200, seed=23)
+    for precision in (0, 1):
+        plan = wfp.Plan(wl.src_xy, None, wl.dt, 200, wl.band_limit, wl.tol, precision=precision)
+        z = np.zeros(wl.M)
+        out = [plan.step(z) for _ in range(200)]
+        assert plan.info()["lag_active"]
+        plan.close()
+        assert not np.any(np.stack(out))
+
+
+def test_isolated_target_has_only_history_contributions():
+    # a target farther than delta from every source has an empty local row
+    wl = inputs.small(80, 3.0, 150, seed=24)
+    tgt = np.array([[1.5, 1.5], [-4.0, -4.0], [9.0, 1.0]])
+    out, info = _run(wl, 150, tgt=tgt)
+    ev = np.array([[x, y, n * wl.dt] for n in (60, 150) for (x, y) in tgt])
+    ref = oracle.field(wl.src_xy, wl.params, ev).reshape(2, -1)
+    got = out[[59, 149]]
+    assert info["n_self"] == 0
+    assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref)

@@ -224,3 +224,16 @@ def test_server_rejects_bad_requests_on_the_host():
     rid2 = ctypes.c_int64()
     assert wfp.lib().wfp_server_submit(sv._h, ctypes.byref(q), ctypes.byref(rid2)) == wfp.WFP_EUNSUPPORTED
     sv.close()
+
+
+def test_fixed_delta_sets_W_and_bounds_are_checked():
+    i = wfp.select_params(10.0, 0.025, 400, 12.7, 1e-6, delta=1.2)
+    assert i["W"] == 48 and i["nmax"] > 32 and i["nmax"] <= 64
+    assert abs(i["delta"] / i["scale"] - 48 * 0.025) < 1e-12
+    with pytest.raises(wfp.WFPError) as ei:
+        wfp.select_params(10.0, 0.025, 400, 12.7, 1e-6, delta=2.0)  # W = 80 > 59
+    assert ei.value.code == wfp.WFP_EINVAL
+    with pytest.raises(wfp.WFPError):
+        wfp.select_params(10.0, 0.1, 400, 12.7, 1e-6, delta=0.3)  # W = 3 violates Eq. dt
+    with pytest.raises(wfp.WFPError):
+        wfp.select_params(10.0, 0.1, 400, 12.7, 1e-6, local_interp=5)
