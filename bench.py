@@ -321,9 +321,10 @@ def roofline(r: dict, M: int, Mt: int, fp64: bool) -> tuple[dict, dict]:
             with open(tj) as f:
                 tr = json.load(f)
             key = f"{dom}:{'fp64' if fp64 else 'mixed'}:{r['workload']}"
+            if dom == "local":  # per variant (the autotuner may pick any of the bit-identical forms)
+                key += f":v{r['info'].get('local_variant')}"
             ent = tr.get(key, {})
-            variant_ok = dom != "local" or ent.get("local_variant") == r["info"].get("local_variant")
-            if ent.get("source_hash") == source_hash(dom) and variant_ok:
+            if ent.get("source_hash") == source_hash(dom):
                 traffic = ent["bytes_per_launch"]
         if e["bound"] == "hbm":
             roof = {"kernel": dom, "bound": "hbm", "achieved": round(e["GB/s"], 1), "peak": peaks["hbm_gbs"],
