@@ -184,11 +184,9 @@ static wfp_status run_phase(Plan& pl, int which, F body, std::string& err) {
     return WFP_OK;
 }
 
-// Enqueue the device work of one step on the plan's stream.
-static wfp_status enqueue_step(Plan& pl, bool do_advance, bool lag_now, cudaEvent_t after_output,
-                               double* u_dev_dst, double* u_host_stage, std::string& err) {
-    wfp_status st = run_phase(pl, 0, [&]() { return step_output(pl, err); }, err);
-    if (st != WFP_OK) return st;
+// The step's output to the caller's device buffer or the pinned host stage, on the plan's stream.
+static wfp_status copy_output(Plan& pl, cudaEvent_t after_output, double* u_dev_dst, double* u_host_stage,
+                              std::string& err) {
     cudaError_t e = cudaSuccess;
     {
         ProfScope ps(pl, PP_COPY);
@@ -206,14 +204,28 @@ static wfp_status enqueue_step(Plan& pl, bool do_advance, bool lag_now, cudaEven
         err = "cudaEventRecord failed";
         return WFP_ECUDA;
     }
-    int which = do_advance ? (lag_now ? 2 : 1) : 3;
-    return run_phase(pl, which, [&]() {
-        if (do_advance) {
-            wfp_status s2 = step_advance_body(pl, lag_now, err);
-            if (s2 != WFP_OK) return s2;
-        }
-        return step_tick(pl, err);
-    }, err);
+    return WFP_OK;
+}
+
+// Enqueue the device work of one step on the plan's stream.
+static wfp_status enqueue_step(Plan& pl, bool do_advance, bool lag_now, cudaEvent_t after_output,
+                               double* u_dev_dst, double* u_host_stage, std::string& err) {
+    const int which = do_advance ? (lag_now ? 2 : 1) : 3;
+    if (!pl.prof) {  // the whole step as one (graph-captured) fork/join of two streams
+        wfp_status st = run_phase(pl, which, [&]() { return step_concurrent(pl, do_advance, lag_now, err); }, err);
+        if (st != WFP_OK) return st;
+        return copy_output(pl, after_output, u_dev_dst, u_host_stage, err);
+    }
+    // profiling: every part in sequence on the plan's stream, each bracketed by events
+    wfp_status st = step_output(pl, err);
+    if (st != WFP_OK) return st;
+    st = copy_output(pl, after_output, u_dev_dst, u_host_stage, err);
+    if (st != WFP_OK) return st;
+    if (do_advance) {
+        st = step_advance_body(pl, lag_now, err);
+        if (st != WFP_OK) return st;
+    }
+    return step_tick(pl, err);
 }
 
 namespace wfp {

@@ -42,7 +42,7 @@ std::vector<Section> sections(const Plan& pl) {
     if (pl.d_ring_lag != pl.d_ring) v.push_back({pl.d_ring_lag, (size_t)pl.R_lag * pl.n_modes * 2 * s});
     if (pl.d_B) v.push_back({pl.d_B, (size_t)P.n_lambda * pl.n_far * 16});
     if (pl.d_Y) v.push_back({pl.d_Y, (size_t)pl.n_soe_self * pl.n_self * 8});
-    v.push_back({pl.d_uh, (size_t)pl.Mt * 8});
+    v.push_back({pl.d_uh, (size_t)pl.Mt * 2 * 8});
     v.push_back({pl.d_step, 8});
     return v;
 }

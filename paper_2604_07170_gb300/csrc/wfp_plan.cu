@@ -706,11 +706,14 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
             pl.d_ring_lag = pl.d_ring;  // the stored history serves both FIRs (or the lag is inactive)
         }
         CK(mem.alloc(&pl.d_uloc, Mt));
-        CK(mem.alloc(&pl.d_uh, Mt));
+        CK(mem.alloc(&pl.d_uh, 2 * Mt));
         CK(mem.alloc(&pl.d_uself, Mt));
         CK(mem.alloc(&pl.d_u_out, Mt));
     }
     CK(mem.alloc(&pl.d_sched, 2));
+    CK(cudaStreamCreateWithFlags(&pl.stream2, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&pl.ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&pl.ev_join, cudaEventDisableTiming));
     CK(cudaHostAlloc(&pl.h_err, sizeof(int), cudaHostAllocMapped));
     *(volatile int*)pl.h_err = 0;
     CK(cudaHostGetDevicePointer((void**)&pl.d_err, pl.h_err, 0));
@@ -873,6 +876,9 @@ void plan_free(Plan& pl) {
     if (pl.h_u) cudaFreeHost(pl.h_u);
     if (pl.h_err) cudaFreeHost(pl.h_err);
     if (pl.ev_out) cudaEventDestroy(pl.ev_out);
+    if (pl.ev_fork) cudaEventDestroy(pl.ev_fork);
+    if (pl.ev_join) cudaEventDestroy(pl.ev_join);
+    if (pl.stream2) cudaStreamDestroy(pl.stream2);
     if (pl.own_stream && pl.stream) cudaStreamDestroy(pl.stream);
 }
 

@@ -38,6 +38,9 @@ struct Plan {
     wfp_opts opts;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // side stream of a step: the local part and self term run on it concurrently with the advance
+    cudaStream_t stream2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool poisoned = false;
     int64_t step = 0;  // completed steps
     int device = 0;
@@ -129,7 +132,7 @@ struct Plan {
 
     // outputs (internal target order)
     double* d_uloc = nullptr;
-    double* d_uh = nullptr;      // u_h at the current step (computed by the previous advance)
+    double* d_uh = nullptr;      // [2][Mt] u_h by step parity: step n reads slot n & 1, its advance writes (n+1) & 1
     double* d_uself = nullptr;
     double* d_u_out = nullptr;   // caller order
 
@@ -202,5 +205,7 @@ void plan_free(Plan& pl);
 wfp_status step_output(Plan& pl, std::string& err);   // ingest, local, self, combine (device)
 wfp_status step_advance_body(Plan& pl, bool lag_now, std::string& err);  // NUFFTs, modes, far, interp
 wfp_status step_tick(Plan& pl, std::string& err);     // advance the device step counter
+// the whole step with the local part and self term on stream2, concurrent with the advance
+wfp_status step_concurrent(Plan& pl, bool do_advance, bool lag_now, std::string& err);
 
 }  // namespace wfp

@@ -106,11 +106,14 @@ __global__ void __launch_bounds__(32 * kSelfGroups) k_self(const int64_t* __rest
     }
 }
 
-__global__ void k_combine(int64_t Mt, const int* __restrict__ tgt_perm, const double* __restrict__ uloc,
-                          const double* __restrict__ uh, const double* __restrict__ uself, double* __restrict__ out) {
+// u(t_n) = u_l + u_h - u_self; u_h(t_n) was written by the advance of step n - 1 into slot n & 1
+__global__ void k_combine(const int64_t* __restrict__ d_step, int64_t Mt, const int* __restrict__ tgt_perm,
+                          const double* __restrict__ uloc, const double* __restrict__ uh,
+                          const double* __restrict__ uself, double* __restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Mt) return;
-    out[tgt_perm[i]] = uloc[i] + uh[i] - uself[i];
+    const int64_t n = *d_step + 1;
+    out[tgt_perm[i]] = uloc[i] + uh[(n & 1) * Mt + i] - uself[i];
 }
 
 __global__ void k_tick(int64_t* d_step) { *d_step += 1; }
@@ -551,13 +554,15 @@ __global__ void __launch_bounds__(32 * kFarGroups) k_far(
 // --------------------------------------------------------------------------- interpolation
 // Type-2 interpolation: u_h(x_i) = sum over the w x w footprint of grid * psi_x psi_y.
 // One warp per target, lane = column offset.
+// u_h(t_{n+1}) goes to slot (n + 1) & 1 of uh, so that step n's output can still read slot n & 1.
 template <typename T>
-__global__ void __launch_bounds__(256) k_interp(int64_t Mt, const int* __restrict__ tgt_off,
-                                                const T* __restrict__ tgt_ker, int w, const T* __restrict__ tf,
-                                                int nf, int lb0, double* __restrict__ uh) {
+__global__ void __launch_bounds__(256) k_interp(const int64_t* __restrict__ d_step, int64_t Mt,
+                                                const int* __restrict__ tgt_off, const T* __restrict__ tgt_ker, int w,
+                                                const T* __restrict__ tf, int nf, int lb0, double* __restrict__ uh) {
     int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (i >= Mt) return;
+    uh += ((*d_step + 2) & 1) * Mt;
     int off = tgt_off[i];
     int ix0 = off & 0xffff, iy0 = off >> 16;
     const T* ker = tgt_ker + i * 2 * w;
@@ -611,14 +616,19 @@ void prof_collect(Plan& pl) {
 }
 
 template <typename T>
-static wfp_status output_t(Plan& pl, std::string& err) {
-    const Params& P = pl.P;
-    cudaStream_t st = pl.stream;
+static wfp_status ingest_t(Plan& pl, std::string& err) {
     ProfScope ps0(pl, PP_INGEST);
-    k_ingest<T><<<nblk(pl.M, 256), 256, 0, st>>>(pl.d_step, pl.M, pl.d_sig_in, pl.d_src_perm, (T*)pl.d_sigwin,
-                                                   pl.NW, (T*)pl.d_siglin, (T*)pl.d_sighist, pl.n_hist);
+    k_ingest<T><<<nblk(pl.M, 256), 256, 0, pl.stream>>>(pl.d_step, pl.M, pl.d_sig_in, pl.d_src_perm,
+                                                          (T*)pl.d_sigwin, pl.NW, (T*)pl.d_siglin, (T*)pl.d_sighist,
+                                                          pl.n_hist);
     CK(cudaGetLastError());
-    ps0.stop();
+    return WFP_OK;
+}
+
+// local part, self term and combine on stream st
+template <typename T>
+static wfp_status localpart_t(Plan& pl, cudaStream_t st, std::string& err) {
+    const Params& P = pl.P;
     if (pl.Mt > 0) {
         ProfScope ps(pl, PP_LOCAL);
         local_run(pl, st);
@@ -626,19 +636,24 @@ static wfp_status output_t(Plan& pl, std::string& err) {
     }
     if (pl.n_self > 0) {
         ProfScope ps(pl, PP_SELF);
-        k_self<T><<<nblk(pl.n_self, 32), dim3(32, kSelfGroups), 0, st>>>(pl.d_step, pl.n_self, pl.d_self_tgt, pl.d_self_src,
-                                                               (const T*)pl.d_sigwin, pl.NW, P.W, pl.n_soe_self,
-                                                               pl.d_shead, pl.d_sdecay, pl.d_sforce, pl.d_sw, pl.d_Y,
-                                                               pl.d_uself);
+        k_self<T><<<nblk(pl.n_self, 32), dim3(32, kSelfGroups), 0, st>>>(
+            pl.d_step, pl.n_self, pl.d_self_tgt, pl.d_self_src, (const T*)pl.d_sigwin, pl.NW, P.W, pl.n_soe_self,
+            pl.d_shead, pl.d_sdecay, pl.d_sforce, pl.d_sw, pl.d_Y, pl.d_uself);
         CK(cudaGetLastError());
     }
     {
         ProfScope ps(pl, PP_COMBINE);
-        k_combine<<<nblk(pl.Mt, 256), 256, 0, st>>>(pl.Mt, pl.d_tgt_perm, pl.d_uloc, pl.d_uh, pl.d_uself,
-                                                    pl.d_u_out);
+        k_combine<<<nblk(pl.Mt, 256), 256, 0, st>>>(pl.d_step, pl.Mt, pl.d_tgt_perm, pl.d_uloc, pl.d_uh,
+                                                    pl.d_uself, pl.d_u_out);
         CK(cudaGetLastError());
     }
     return WFP_OK;
+}
+
+template <typename T>
+static wfp_status output_t(Plan& pl, std::string& err) {
+    wfp_status s = ingest_t<T>(pl, err);
+    return s != WFP_OK ? s : localpart_t<T>(pl, pl.stream, err);
 }
 
 template <typename T>
@@ -752,8 +767,8 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err) {
     }
     ps2.stop();
     ProfScope psi(pl, PP_INTERP);
-    k_interp<T><<<nblk(pl.Mt * 32, 256), 256, 0, st>>>(pl.Mt, pl.d_tgt_off, (const T*)pl.d_tgt_ker, P.w,
-                                                       (const T*)pl.d_tf, P.nf, P.lb0, pl.d_uh);
+    k_interp<T><<<nblk(pl.Mt * 32, 256), 256, 0, st>>>(pl.d_step, pl.Mt, pl.d_tgt_off, (const T*)pl.d_tgt_ker,
+                                                       P.w, (const T*)pl.d_tf, P.nf, P.lb0, pl.d_uh);
     CK(cudaGetLastError());
     return WFP_OK;
 }
@@ -770,6 +785,32 @@ wfp_status step_tick(Plan& pl, std::string& err) {
     k_tick<<<1, 1, 0, pl.stream>>>(pl.d_step);
     CK(cudaGetLastError());
     return WFP_OK;
+}
+
+// One whole step: ingest on the plan's stream, then the local part / self term / combine on the
+// side stream concurrently with the advance (spreading, FFTs, modes, far history, interpolation) on
+// the plan's stream; both join before the step counter moves.  The two branches share no written
+// buffer: u_h is double-buffered by step parity.
+template <typename T>
+static wfp_status concurrent_t(Plan& pl, bool do_advance, bool lag_now, std::string& err) {
+    wfp_status s = ingest_t<T>(pl, err);
+    if (s != WFP_OK) return s;
+    CK(cudaEventRecord(pl.ev_fork, pl.stream));
+    CK(cudaStreamWaitEvent(pl.stream2, pl.ev_fork, 0));
+    s = localpart_t<T>(pl, pl.stream2, err);
+    if (s != WFP_OK) return s;
+    CK(cudaEventRecord(pl.ev_join, pl.stream2));
+    if (do_advance) {
+        s = advance_t<T>(pl, lag_now, err);
+        if (s != WFP_OK) return s;
+    }
+    CK(cudaStreamWaitEvent(pl.stream, pl.ev_join, 0));
+    return step_tick(pl, err);
+}
+
+wfp_status step_concurrent(Plan& pl, bool do_advance, bool lag_now, std::string& err) {
+    return pl.P.precision == WFP_FP64 ? concurrent_t<double>(pl, do_advance, lag_now, err)
+                                      : concurrent_t<float>(pl, do_advance, lag_now, err);
 }
 
 }  // namespace wfp
