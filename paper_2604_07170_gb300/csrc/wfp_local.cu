@@ -284,7 +284,7 @@ static void bulk_one(const Plan& pl, cudaStream_t st) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_local_bulk<T, CH, S, WARPS>, WARPS * 32, G::SMEM);
-        fit = std::max(1, sms * std::max(per, 1));
+        fit = std::max(1, sms * std::max(per - 1, 1));  // one CTA slot per SM left to the advance stream
     }
     const int64_t need = (pl.Mt + WARPS - 1) / WARPS;
     k_local_bulk<T, CH, S, WARPS><<<(unsigned)std::min<int64_t>(need, fit), WARPS * 32, G::SMEM, st>>>(
