@@ -514,6 +514,12 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(upload(mem, &pl.d_fdecay, fdec));
         CK(upload(mem, &pl.d_fforce, ffor));
         CK(mem.alloc(&pl.d_B, (size_t)P.n_lambda * pl.n_far));
+        CK(mem.alloc(&pl.d_aF, (size_t)pl.n_far));
+        for (size_t f = 0; f < fm.size(); f++)
+            if (fm[f] != (int)f) {  // modes are ordered by |k|, so the far modes are a prefix
+                err = "far modes are not the first modes";
+                return WFP_ECUDA;
+            }
         CK(cudaStreamSynchronize(cudaStreamPerThread));
     }
 
@@ -712,6 +718,8 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
     }
     CK(mem.alloc(&pl.d_sched, 2));
     CK(cudaStreamCreateWithFlags(&pl.stream2, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&pl.stream3, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&pl.ev_far, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&pl.ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&pl.ev_join, cudaEventDisableTiming));
     CK(cudaHostAlloc(&pl.h_err, sizeof(int), cudaHostAllocMapped));
@@ -878,7 +886,9 @@ void plan_free(Plan& pl) {
     if (pl.ev_out) cudaEventDestroy(pl.ev_out);
     if (pl.ev_fork) cudaEventDestroy(pl.ev_fork);
     if (pl.ev_join) cudaEventDestroy(pl.ev_join);
+    if (pl.ev_far) cudaEventDestroy(pl.ev_far);
     if (pl.stream2) cudaStreamDestroy(pl.stream2);
+    if (pl.stream3) cudaStreamDestroy(pl.stream3);
     if (pl.own_stream && pl.stream) cudaStreamDestroy(pl.stream);
 }
 

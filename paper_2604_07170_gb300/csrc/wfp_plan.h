@@ -40,7 +40,8 @@ struct Plan {
     bool own_stream = false;
     // side stream of a step: the local part and self term run on it concurrently with the advance
     cudaStream_t stream2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t stream3 = nullptr;  // far history (stored S history only)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_far = nullptr;
     bool poisoned = false;
     int64_t step = 0;  // completed steps
     int device = 0;
@@ -118,6 +119,7 @@ struct Plan {
     double* d_fdecay = nullptr;  // [n_lambda] r_l = exp(-lambda_l dt)
     double* d_fforce = nullptr;  // [n_lambda] a_l r_l^(W-1): weight of S_{n-L-W+1} in the tail recurrence
     double2* d_B = nullptr;      // [n_lambda][n_far] tail state E_l (scaled by exp(A lambda_l), Eq. beta0)
+    double2* d_aF = nullptr;     // [n_far] alpha_F of the current step, added by the mode update
 
     // self term of coincident pairs
     int64_t n_self = 0;

@@ -219,7 +219,8 @@ __global__ void __launch_bounds__(256) k_modes(
     typename Cplx<T>::type* __restrict__ ring, typename Cplx<T>::type* __restrict__ ring_lag, int R_cur, int R_lag,
     int lag_off, int write_lag,
     const T* __restrict__ taps, const double* __restrict__ rot, double2* __restrict__ alpha,
-    double2* __restrict__ alphad, typename Cplx<T>::type* __restrict__ td, int64_t near_sq) {
+    double2* __restrict__ alphad, typename Cplx<T>::type* __restrict__ td, int64_t near_sq,
+    const double2* __restrict__ aF, int64_t n_far_now) {
     using C = typename Cplx<T>::type;
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n_modes) return;
@@ -246,13 +247,18 @@ __global__ void __launch_bounds__(256) k_modes(
         ring_lag[(int64_t)((n - L + lag_off) % R_lag) * n_modes + m] = s;
     }
     // the near history is truncated at |k| <= K (Eq. uhtraptrunc); modes between K and the far
-    // cut-off carry only S (for the far forcing) and the far coefficient added by k_far
+    // cut-off carry only S (for the far forcing) and the far coefficient alpha_F
+    const double2 af = (m < n_far_now) ? aF[m] : make_double2(0.0, 0.0);
     if ((int64_t)nn.x * nn.x + (int64_t)nn.y * nn.y > near_sq) {
+        const double cf = coef2 * f;
         C o;
-        o.x = 0;
-        o.y = 0;
+        o.x = (T)(af.x * cf);
+        o.y = (T)(-af.y * cf);
         td[gi] = o;
-        if (nn.y == 0 && nn.x > 0) td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
+        if (nn.y == 0 && nn.x > 0) {
+            o.y = (T)(af.y * cf);
+            td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
+        }
         return;
     }
     // levels n - j (ring slot sl) and n - L - j (ring_lag slot sll), j = 0..W-1, taken U at a time
@@ -312,12 +318,12 @@ __global__ void __launch_bounds__(256) k_modes(
     alpha[m] = an;
     alphad[m] = adn;
     double cf = coef2 * f;
-    C o;
-    o.x = (T)(an.x * cf);
-    o.y = (T)(-an.y * cf);
+    C o;  // type-2 coefficient of the near plus far history
+    o.x = (T)((an.x + af.x) * cf);
+    o.y = (T)(-(an.y + af.y) * cf);
     td[gi] = o;
     if (nn.y == 0 && nn.x > 0) {
-        o.y = (T)(an.y * cf);
+        o.y = (T)((an.y + af.y) * cf);
         td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
     }
 }
@@ -334,7 +340,8 @@ __global__ void __launch_bounds__(256) k_modes_pair(
     const int* __restrict__ mode_k, const float* __restrict__ facf, float coef2, const float2* __restrict__ tc_cur,
     const float2* __restrict__ tc_lag, float2* __restrict__ ring, float2* __restrict__ ring_lag, int R_cur, int R_lag,
     int lag_off, int write_lag, const float* __restrict__ taps, const double* __restrict__ rot,
-    double2* __restrict__ alpha, double2* __restrict__ alphad, float2* __restrict__ td, int64_t near_sq) {
+    double2* __restrict__ alpha, double2* __restrict__ alphad, float2* __restrict__ td, int64_t near_sq,
+    const double2* __restrict__ aF, int64_t n_far_now) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t m = tid >> 1;
     const int r = (int)(tid & 1);
@@ -422,11 +429,18 @@ __global__ void __launch_bounds__(256) k_modes_pair(
     }
     const double vx = (double)xh + (double)xl, vy = (double)yh + (double)yl;  // h (r = 0) or g (r = 1)
     if (!valid) return;
-    if (!near) {
+    const float cf = coef2 * f;  // type-2 coefficient in the grid precision
+    if (!near) {  // only the far coefficient alpha_F, if any
         if (r == 0) {
-            float2 o = make_float2(0.f, 0.f);
+            const double2 af = (m < n_far_now) ? aF[m] : make_double2(0.0, 0.0);
+            float2 o;
+            o.x = (float)af.x * cf;
+            o.y = -(float)af.y * cf;
             td[gi] = o;
-            if (nn.y == 0 && nn.x > 0) td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
+            if (nn.y == 0 && nn.x > 0) {
+                o.y = (float)af.y * cf;
+                td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
+            }
         }
         return;
     }
@@ -437,7 +451,11 @@ __global__ void __launch_bounds__(256) k_modes_pair(
         an.x = fma(c, a.x, fma(sk, ad.x, vx));
         an.y = fma(c, a.y, fma(sk, ad.y, vy));
         alpha[m] = an;
-        const float cf = coef2 * f;  // type-2 coefficient in the grid precision
+        if (m < n_far_now) {  // near plus far history
+            const double2 af = aF[m];
+            an.x += af.x;
+            an.y += af.y;
+        }
         float2 o;
         o.x = (float)an.x * cf;
         o.y = -(float)an.y * cf;
@@ -459,34 +477,56 @@ __global__ void __launch_bounds__(256) k_modes_pair(
 // trapezoid interpolant of the lagged S on the grid (exp(A lam) scaling carried in the state):
 //   E_l(t_{n+1}) = r_l E_l(t_n) + f_l S_{n-L-W+1}                  (tail recurrence, one tap)
 //   alpha_F = sum_l H_l(|k|) E_l + sum_{q<W-1} Phi_q(|k|) S_{n-L-q}   (Eq. alphaFApprox + newest levels)
-// alpha_F is added to the type-2 coefficient written by k_modes.  Block (32, G): 32 far modes x G
-// groups of terms; the W newest lagged levels of the block's modes are staged in shared memory.
-// H and Phi are stored [term][|k|], so the 32 modes of a warp (ordered by |k|) read neighbours.
+// alpha_F goes to aF_out; the mode update adds it to the type-2 coefficient.  With the S history
+// stored every level read here is at least L steps old, so the kernel can run while this step's
+// type-1 transform is computed; with the lag recomputed the newest lagged level n - L is taken from
+// this step's lagged transform and deconvolved exactly as the mode update does.  Block (32, G): 32
+// far modes x G groups of terms; the W newest lagged levels of the block's modes are staged in
+// shared memory.  Far modes are the first n_far modes (modes are ordered by |k|); H and Phi are
+// stored [term][|k|], so the 32 modes of a warp read neighbours.
 constexpr int kFarGroups = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kFarGroups) k_far(
     const int64_t* __restrict__ d_step, int64_t n_far, int64_t n_modes, int W, int L, int Nh, int nf, int nlam,
-    int64_t n_fk, const int* __restrict__ far_mode, const int* __restrict__ far_k, const int2* __restrict__ mode_n,
-    const double* __restrict__ fac, double coef2, const typename Cplx<T>::type* __restrict__ ring_lag, int R_lag,
-    int lag_off, const double* __restrict__ H, const double* __restrict__ ffir, const double* __restrict__ fdecay,
-    const double* __restrict__ fforce, double2* __restrict__ B, typename Cplx<T>::type* __restrict__ td) {
+    int64_t n_fk, const int* __restrict__ far_k, const int2* __restrict__ mode_n, const double* __restrict__ fac,
+    const float* __restrict__ facf, const typename Cplx<T>::type* __restrict__ tc_lag, int from_tc,
+    const typename Cplx<T>::type* __restrict__ ring_lag, int R_lag, int lag_off, const double* __restrict__ H,
+    const double* __restrict__ ffir, const double* __restrict__ fdecay, const double* __restrict__ fforce,
+    double2* __restrict__ B, double2* __restrict__ aF_out) {
     using C = typename Cplx<T>::type;
     constexpr int G = kFarGroups;
     int64_t n = *d_step + 1;
     if (n - L < 1) return;
     __shared__ double2 s_red[G][32];
     __shared__ C s_S[kMaxWFar][32];
-    int64_t f = (int64_t)blockIdx.x * 32 + threadIdx.x;
-    int g = threadIdx.y;
-    bool valid = f < n_far;
-    int64_t m = valid ? far_mode[f] : 0;
+    const int64_t f = (int64_t)blockIdx.x * 32 + threadIdx.x;  // far mode f is mode f
+    const int g = threadIdx.y;
+    const bool valid = f < n_far;
     for (int j = g; j < W; j += G) {
-        int sl = (int)((((n - L - j + lag_off) % R_lag) + R_lag) % R_lag);  // level n - L - j
-        C z;
-        z.x = 0;
-        z.y = 0;
-        s_S[j][threadIdx.x] = valid ? ring_lag[(int64_t)sl * n_modes + m] : z;
+        C v;
+        v.x = 0;
+        v.y = 0;
+        if (valid) {
+            if (j == 0 && from_tc) {  // level n - L from this step's lagged transform
+                const int2 nn = mode_n[f];
+                const int row = nn.x < 0 ? nn.x + nf : nn.x;
+                const C t = tc_lag[(int64_t)row * (Nh + 1) + nn.y];
+                if constexpr (sizeof(T) == 8) {
+                    const double fd = fac[nn.x < 0 ? -nn.x : nn.x] * fac[nn.y];
+                    v.x = (T)((double)t.x * fd);
+                    v.y = (T)(-(double)t.y * fd);
+                } else {
+                    const float ff = facf[nn.x < 0 ? -nn.x : nn.x] * facf[nn.y];
+                    v.x = t.x * ff;
+                    v.y = -t.y * ff;
+                }
+            } else {
+                const int sl = (int)((((n - L - j + lag_off) % R_lag) + R_lag) % R_lag);  // level n - L - j
+                v = ring_lag[(int64_t)sl * n_modes + f];
+            }
+        }
+        s_S[j][threadIdx.x] = v;
     }
     __syncthreads();
     double2 aF = make_double2(0.0, 0.0);
@@ -533,21 +573,7 @@ __global__ void __launch_bounds__(32 * kFarGroups) k_far(
             aF.x += s_red[k][threadIdx.x].x;
             aF.y += s_red[k][threadIdx.x].y;
         }
-        int2 nn = mode_n[m];
-        int row = nn.x < 0 ? nn.x + nf : nn.x;
-        int64_t gi = (int64_t)row * (Nh + 1) + nn.y;
-        double cf = coef2 * fac[nn.x < 0 ? -nn.x : nn.x] * fac[nn.y];
-        C o = td[gi];
-        o.x = (T)((double)o.x + aF.x * cf);
-        o.y = (T)((double)o.y - aF.y * cf);
-        td[gi] = o;
-        if (nn.y == 0 && nn.x > 0) {
-            int64_t gp = (int64_t)(nf - nn.x) * (Nh + 1);
-            C q = td[gp];
-            q.x = (T)((double)q.x + aF.x * cf);
-            q.y = (T)((double)q.y + aF.y * cf);
-            td[gp] = q;
-        }
+        aF_out[f] = aF;
     }
 }
 
@@ -689,7 +715,23 @@ wfp_status exec_c2r<float>(cufftHandle h, float2* in, float* out) {
 }
 
 template <typename T>
-static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err) {
+static wfp_status far_t(Plan& pl, cudaStream_t st, std::string& err) {
+    using C = typename Cplx<T>::type;
+    const Params& P = pl.P;
+    ProfScope ps(pl, PP_FAR);
+    dim3 blk(32, kFarGroups);
+    k_far<T><<<nblk(pl.n_far, 32), blk, 0, st>>>(
+        pl.d_step, pl.n_far, pl.n_modes, P.W, P.L, P.Nh, P.nf, P.n_lambda, pl.n_fkappa, pl.d_far_k, pl.d_mode_n,
+        pl.d_fac, pl.d_facf, (const C*)pl.d_tc_lag, pl.lag_store ? 0 : 1, (const C*)pl.d_ring_lag, pl.R_lag,
+        pl.lag_off, pl.d_H, pl.d_ffir, pl.d_fdecay, pl.d_fforce, pl.d_B, pl.d_aF);
+    CK(cudaGetLastError());
+    return WFP_OK;
+}
+
+// far_elsewhere: the far history of this step was enqueued on another stream (it only reads stored
+// levels) and the caller has made this stream wait for it before the mode update
+template <typename T>
+static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err, cudaEvent_t far_done = nullptr) {
     using C = typename Cplx<T>::type;
     const Params& P = pl.P;
     cudaStream_t st = pl.stream;
@@ -724,6 +766,16 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err) {
         }
     }
     psf.stop();
+    const bool far_now = lag_now && P.far_active && pl.n_far > 0;
+    if (far_now) {
+        if (far_done) {
+            CK(cudaStreamWaitEvent(st, far_done, 0));
+        } else {
+            wfp_status sf = far_t<T>(pl, st, err);
+            if (sf != WFP_OK) return sf;
+        }
+    }
+    const int64_t n_far_now = far_now ? pl.n_far : 0;
     double coef2 = (P.dk / (2 * kPi)) * (P.dk / (2 * kPi));
     ProfScope psm(pl, PP_MODES);
     const int64_t near_sq = (int64_t)std::floor((P.K / P.dk) * (P.K / P.dk));
@@ -732,26 +784,17 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err) {
             pl.d_step, pl.n_modes, P.W, P.L, P.Nh, P.nf, pl.d_mode_n, pl.d_mode_k, pl.d_fac, coef2,
             (const C*)pl.d_tc_cur, (const C*)pl.d_tc_lag, (C*)pl.d_ring, (C*)pl.d_ring_lag, pl.R_cur, pl.R_lag,
             pl.lag_off, pl.lag_store ? 0 : 1, (const T*)pl.d_taps, pl.d_rot, pl.d_alpha, pl.d_alphad, (C*)pl.d_td,
-            near_sq);
+            near_sq, pl.d_aF, n_far_now);
     } else {
         auto kern = pl.compact_taps ? k_modes_pair<true> : k_modes_pair<false>;
         kern<<<nblk(2 * pl.n_modes, 256), 256, 0, st>>>(
             pl.d_step, pl.n_modes, P.W, P.L, P.Nh, P.nf, pl.d_mode_n, pl.d_mode_k, pl.d_facf, (float)coef2,
             (const float2*)pl.d_tc_cur, (const float2*)pl.d_tc_lag, (float2*)pl.d_ring, (float2*)pl.d_ring_lag,
             pl.R_cur, pl.R_lag, pl.lag_off, pl.lag_store ? 0 : 1, (const float*)pl.d_taps, pl.d_rot, pl.d_alpha,
-            pl.d_alphad, (float2*)pl.d_td, near_sq);
+            pl.d_alphad, (float2*)pl.d_td, near_sq, pl.d_aF, n_far_now);
     }
     CK(cudaGetLastError());
     psm.stop();
-    if (lag_now && P.far_active && pl.n_far > 0) {
-        ProfScope ps(pl, PP_FAR);
-        dim3 blk(32, kFarGroups);
-        k_far<T><<<nblk(pl.n_far, 32), blk, 0, st>>>(pl.d_step, pl.n_far, pl.n_modes, P.W, P.L, P.Nh, P.nf,
-                                                      P.n_lambda, pl.n_fkappa, pl.d_far_mode, pl.d_far_k, pl.d_mode_n,
-                                                      pl.d_fac, coef2, (const C*)pl.d_ring_lag, pl.R_lag, pl.lag_off,
-                                                      pl.d_H, pl.d_ffir, pl.d_fdecay, pl.d_fforce, pl.d_B, (C*)pl.d_td);
-        CK(cudaGetLastError());
-    }
     // type-2: columns (C2C, inverse) then band rows (C2R); the C2R input beyond column Nh is re-zeroed
     ProfScope ps2(pl, PP_FFT2);
     if (exec_c2c<T>(pl.fftBi, (C*)pl.d_td, (C*)pl.d_te, CUFFT_INVERSE) != WFP_OK) {
@@ -801,7 +844,16 @@ static wfp_status concurrent_t(Plan& pl, bool do_advance, bool lag_now, std::str
     if (s != WFP_OK) return s;
     CK(cudaEventRecord(pl.ev_join, pl.stream2));
     if (do_advance) {
-        s = advance_t<T>(pl, lag_now, err);
+        // with the S history stored the far history reads only old levels: a third branch
+        cudaEvent_t far_done = nullptr;
+        if (lag_now && pl.P.far_active && pl.n_far > 0 && pl.lag_store) {
+            CK(cudaStreamWaitEvent(pl.stream3, pl.ev_fork, 0));
+            s = far_t<T>(pl, pl.stream3, err);
+            if (s != WFP_OK) return s;
+            CK(cudaEventRecord(pl.ev_far, pl.stream3));
+            far_done = pl.ev_far;
+        }
+        s = advance_t<T>(pl, lag_now, err, far_done);
         if (s != WFP_OK) return s;
     }
     CK(cudaStreamWaitEvent(pl.stream, pl.ev_join, 0));
