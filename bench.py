@@ -338,6 +338,23 @@ def roofline(r: dict, M: int, Mt: int, fp64: bool) -> tuple[dict, dict]:
     return roof, per
 
 
+def parts_roofline(per: dict, fp64: bool) -> dict:
+    """Each timed part against its own bound (algorithmic bytes / flops per launch over its
+    event-timed launch, in sequence): HBM against the measured copy bandwidth, ALU against the
+    derived FP64 (FP64 path) or FP32 peak."""
+    peaks = measured_peaks()
+    alu = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+    out = {}
+    for k, e in per.items():
+        if "bound" not in e:
+            continue
+        if e["bound"] == "hbm":
+            out[k] = {"bound": "hbm", "GB/s": round(e["GB/s"], 1), "frac": round(e["GB/s"] / peaks["hbm_gbs"], 3)}
+        else:
+            out[k] = {"bound": "alu", "TFLOP/s": round(e["TFLOP/s"], 4), "frac": round(e["TFLOP/s"] / alu, 3)}
+    return out
+
+
 def source_hash(kernel: str = "local") -> str:
     """Hash of the sources a kernel is built from (its counters go stale when they change)."""
     import hashlib
@@ -411,16 +428,17 @@ def serve(args):
             raise RuntimeError(f"requests failed: {bad}")
         lat = np.array([q["t_done"] - q["t_submit"] for q in st])
         wait = np.array([q["t_admit"] - q["t_submit"] for q in st])
+        build = np.array([q["t_active"] - q["t_admit"] for q in st])
         span = max(q["t_done"] for q in st) - min(q["t_submit"] for q in st)
-        return lat, wait, span, clk.summary()
+        return lat, wait, span, clk.summary(), build
 
-    lat_b, _, span_b, _ = run(np.zeros(len(reqs)))
+    lat_b, _, span_b, _, build_b = run(np.zeros(len(reqs)))
     cap = work.sum() / span_b
     lam = args.serve_load * cap / work.mean()
     rng = np.random.default_rng(inputs.SEED0 + 5)
     arr = np.cumsum(rng.exponential(1.0 / lam, len(reqs)))
     arr -= arr[0]
-    lat, wait, span, clocks = run(arr)
+    lat, wait, span, clocks, build = run(arr)
     line = {
         "metric": "serving target-updates/s and request latency (Poisson arrivals)",
         "value": work.sum() / span, "unit": "target-updates/s", "n_gpus": 1, "steps": len(reqs), "warmup": 0,
@@ -435,6 +453,7 @@ def serve(args):
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "max": float(lat.max())},
         "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+        "plan_build_s": {"p50": float(np.percentile(build, 50)), "max": float(build.max()), "sum": float(build.sum())},
         "makespan_s": span, "clocks": clocks,
     }
     print(json.dumps(line))
@@ -497,6 +516,7 @@ def main():
         "fft_time_share": round(fft_ms / tot_ms, 4) if tot_ms else None,
         "parts_ms_per_step": {k: round(v["ms_per_launch"] * v["launches"] / r["prof_steps"], 5)
                               for k, v in parts.items()},
+        "parts_roofline": parts_roofline(parts, fp64),
     }
     if "e2e_s" in r:
         line["e2e"] = {"value": wl.M * r["e2e_steps"] / r["e2e_s"], "unit": "target-updates/s",
@@ -505,7 +525,7 @@ def main():
         m = res["mixed"]
         roof_m, parts_m = roofline(m, wl.M, wl.M, False)
         line["mixed"] = {"value": world * wl.M * m["K"] / (m["ms"] * 1e-3), "ms_per_step": m["ms"] / m["K"],
-                         "roofline": roof_m,
+                         "roofline": roof_m, "parts_roofline": parts_roofline(parts_m, False),
                          "parts_ms_per_step": {k: round(v["ms_per_launch"] * v["launches"] / m["prof_steps"], 5)
                                                for k, v in parts_m.items()}}
     if not args.no_cpu:

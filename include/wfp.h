@@ -275,11 +275,12 @@ wfp_status wfp_local_noalloc(int64_t M, const double* src_xy, int64_t Mt, const 
  *      requests are admitted at once; a request larger than the whole budget fails.  An admitted
  *      request's plan is built on a worker thread (WFP_REQ_BUILDING) while the active requests
  *      keep stepping; it joins the active set on the first tick after its build completes;
- *   2. enqueues one step of every active request, each on its own stream, so that kernels of
- *      different requests overlap on the device; the host runs at most two steps ahead of the
- *      device per request (before enqueueing step n it waits for step n - 2);
- *   3. retires requests that took their last step (it waits for that step, copies the result to
- *      host memory and frees the request's device memory).
+ *   2. enqueues steps of every active request, each on its own stream, so that kernels of
+ *      different requests overlap on the device; a request may have up to four steps in flight
+ *      (step n is enqueued once step n - 4 has completed, asked without blocking), so each
+ *      request advances at its own pace;
+ *   3. retires requests whose last step has completed (copies the result to host memory and frees
+ *      the request's device memory).
  * A request's outputs are bitwise the same whether it runs alone or among others.
  * Not thread-safe: one thread drives a server.
  * ------------------------------------------------------------------------------------------ */
@@ -318,6 +319,7 @@ typedef struct {
     double t_submit, t_admit, t_done;  /* host steady-clock seconds (same clock for all requests) */
     int64_t device_bytes;         /* footprint used for admission (estimate) */
     int64_t plan_bytes;           /* device memory the plan actually held (0 before admission) */
+    double t_active;              /* when its plan was built and it started stepping (0 before) */
 } wfp_request_status;
 
 /* Create a server.  opts (NULL for defaults) apply to every request, except lag_mode and stream,

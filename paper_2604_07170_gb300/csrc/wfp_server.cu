@@ -6,9 +6,9 @@
 // of the server's HBM budget (first fit in arrival order), building each one's plan on its own
 // stream; (2) enqueues one step of every active request, each on its own stream, so that the
 // kernels of small requests overlap on the device; (3) retires the
-// requests that reached N_t, returning their memory to the budget.  The host runs at most two
-// steps ahead of the device per request (an event per step), so it does not wait for a whole
-// round before enqueueing the next.  Each request's Fourier
+// requests that reached N_t, returning their memory to the budget.  The host never waits on a
+// request: each may run up to four steps ahead of the device (an event per step, queried without
+// blocking), so each request advances at its own pace.  Each request's Fourier
 // history stays resident on the device between ticks.  Plans are independent and their kernels
 // deterministic, so a request's result does not depend on what else is being served.
 #include <cuda_runtime.h>
@@ -78,9 +78,9 @@ struct Request {
     std::vector<double> result;
     int64_t steps_done = 0;
     int64_t bytes = 0, plan_bytes = 0;
-    double t_submit = 0, t_admit = 0, t_done = 0;
+    double t_submit = 0, t_admit = 0, t_active = 0, t_done = 0;
     std::string err;
-    cudaEvent_t ev[2] = {nullptr, nullptr};  // completion of the last two enqueued steps
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // completion of the last enqueued steps
     // plan building on a worker thread (the builder writes plan, buffers, build_status and err,
     // then sets build_done; the server thread reads them only after seeing build_done)
     std::thread builder;
@@ -179,7 +179,7 @@ struct wfp_server_s {
     std::deque<Request*> pending;
     std::vector<Request*> building;  // admitted, plan being built on a worker thread
     std::vector<Request*> active;
-    int max_builders = 1;
+    int max_builders = 3;
     std::map<int64_t, std::unique_ptr<Request>> all;
     int device = 0;
 };
@@ -362,36 +362,47 @@ wfp_status wfp_server_tick(wfp_server sv, int* n_active, int* n_pending) {
         wfp_plan_get_info(r->plan, &info);
         r->plan_bytes = info.device_bytes;
         r->state = WFP_REQ_ACTIVE;
+        r->t_active = now_s();
         sv->active.push_back(r);
     }
-    // (2) enqueue one step of every active request on its own stream.  At most two steps of a
-    // request are in flight: before enqueueing step n the host waits for step n - 2.
+    // (2) enqueue steps of every active request on its own stream without waiting: a request may
+    // have up to kInFlight steps in flight (step n is enqueued once step n - kInFlight has completed,
+    // which is asked with a non-blocking query), so small requests are not held to the pace of the
+    // large ones sharing the device
+    constexpr int kInFlight = 4;
     for (Request* r : sv->active) {
         Plan& pl = plan_of(r->plan);
-        const int64_t n = r->steps_done + 1;
-        cudaEvent_t ev = r->ev[n & 1];
-        std::string err;
-        if (n > 2 && cudaEventSynchronize(ev) != cudaSuccess) {
-            r->err = "a step of this request failed on the device";
-            r->state = WFP_REQ_FAILED;
-            continue;
+        for (int k = 0; k < kInFlight && r->steps_done < r->Nt; k++) {
+            const int64_t n = r->steps_done + 1;
+            cudaEvent_t ev = r->ev[n % kInFlight];
+            std::string err;
+            if (n > kInFlight) {
+                const cudaError_t q = cudaEventQuery(ev);
+                if (q == cudaErrorNotReady) break;
+                if (q != cudaSuccess) {
+                    r->err = "a step of this request failed on the device";
+                    r->state = WFP_REQ_FAILED;
+                    break;
+                }
+            }
+            if (r->family == WFP_SIGNAL_ERF)
+                k_gen_erf<<<(unsigned)((r->M + 255) / 256), 256, 0, pl.stream>>>(r->M, r->d_par, n * r->dt,
+                                                                                  pl.d_sig_in);
+            else
+                k_gen_gauss3<<<(unsigned)((r->M + 255) / 256), 256, 0, pl.stream>>>(r->M, r->d_par, n * r->dt,
+                                                                                     pl.d_sig_in);
+            double* dst = nullptr;
+            auto pos = std::lower_bound(r->out_steps.begin(), r->out_steps.end(), n);
+            if (pos != r->out_steps.end() && *pos == n) dst = r->d_out + (pos - r->out_steps.begin()) * r->Mt;
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess || plan_step_device(pl, dst, err) != WFP_OK ||
+                cudaEventRecord(ev, pl.stream) != cudaSuccess) {
+                r->err = err.empty() ? std::string("step launch failed: ") + cudaGetErrorString(e) : err;
+                r->state = WFP_REQ_FAILED;
+                break;
+            }
+            r->steps_done = n;
         }
-        if (r->family == WFP_SIGNAL_ERF)
-            k_gen_erf<<<(unsigned)((r->M + 255) / 256), 256, 0, pl.stream>>>(r->M, r->d_par, n * r->dt, pl.d_sig_in);
-        else
-            k_gen_gauss3<<<(unsigned)((r->M + 255) / 256), 256, 0, pl.stream>>>(r->M, r->d_par, n * r->dt,
-                                                                                 pl.d_sig_in);
-        double* dst = nullptr;
-        auto pos = std::lower_bound(r->out_steps.begin(), r->out_steps.end(), n);
-        if (pos != r->out_steps.end() && *pos == n) dst = r->d_out + (pos - r->out_steps.begin()) * r->Mt;
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess || plan_step_device(pl, dst, err) != WFP_OK ||
-            cudaEventRecord(ev, pl.stream) != cudaSuccess) {
-            r->err = err.empty() ? std::string("step launch failed: ") + cudaGetErrorString(e) : err;
-            r->state = WFP_REQ_FAILED;
-            continue;
-        }
-        r->steps_done = n;
     }
     // (3) retire failed requests and those that took their last step
     for (size_t i = 0; i < sv->active.size();) {
@@ -402,6 +413,12 @@ wfp_status wfp_server_tick(wfp_server sv, int* n_active, int* n_pending) {
             continue;
         }
         if (r->steps_done >= r->Nt) {
+            // retire once the last step has completed (non-blocking check)
+            const cudaError_t q = cudaEventQuery(r->ev[r->Nt % 4]);
+            if (q == cudaErrorNotReady) {
+                i++;
+                continue;
+            }
             int state = WFP_REQ_DONE;
             r->result.resize(r->out_steps.size() * r->Mt);
             if (cudaStreamSynchronize(plan_of(r->plan).stream) != cudaSuccess ||
@@ -451,6 +468,7 @@ wfp_status wfp_server_query(wfp_server sv, int64_t id, wfp_request_status* st) {
     st->t_submit = r.t_submit;
     st->t_admit = r.t_admit;
     st->t_done = r.t_done;
+    st->t_active = r.t_active;
     st->device_bytes = r.bytes;
     st->plan_bytes = r.plan_bytes;
     return WFP_OK;

@@ -72,7 +72,7 @@ class wfp_request(ctypes.Structure):
 class wfp_request_status(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int), ("steps_done", _c_i64), ("Nt", _c_i64), ("Mt", _c_i64),
                 ("n_out", ctypes.c_int), ("t_submit", _c_dbl), ("t_admit", _c_dbl), ("t_done", _c_dbl),
-                ("device_bytes", _c_i64), ("plan_bytes", _c_i64)]
+                ("device_bytes", _c_i64), ("plan_bytes", _c_i64), ("t_active", _c_dbl)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
