@@ -174,6 +174,12 @@ def part_model(info: dict, M: int, Mt: int, fp64: bool) -> dict:
     # E_l read+write (FP64 complex) and H_l per term, W lagged levels, grid read+write
     m["far"] = (nf_ * (nl * (32 + 8) + W * c + 2 * c), nf_ * (nl * 8 + 4 * W))
     m["interp"] = (nb * nb * s + Mt * (2 * w * s + 4 + 8), 2 * Mt * w * w)
+    # two-stage pruned FFTs: R2C over the nb band rows, C2C over the N_h + 1 kept columns (and back)
+    nh2, nc1, lg = nfg // 2 + 1, info["Nh"] + 1, math.log2(nfg)
+    fft_b = nb * nfg * s + nb * nh2 * c + 2 * nfg * nc1 * c
+    fft_f = nb * 2.5 * nfg * lg + nc1 * 5 * nfg * lg
+    m["fft_type1"] = (spreads * fft_b, spreads * fft_f)
+    m["fft_type2"] = (fft_b, fft_f)
     return {k: {"bytes": int(b), "flops": int(f)} for k, (b, f) in m.items()}
 
 
