@@ -316,7 +316,7 @@ def roofline(r: dict, M: int, Mt: int, fp64: bool) -> tuple[dict, dict]:
             tb, tf = b / (peaks["hbm_gbs"] * 1e9), f / (alu_peak * 1e12)
             e["bound"] = "hbm" if tb >= tf else "alu"
         per[name] = e
-    ours = {k: v for k, v in per.items() if k in model}
+    ours = {k: v for k, v in per.items() if k in model and not k.startswith("fft")}  # our kernels, not cuFFT's
     dom = max(ours, key=lambda k: ours[k]["ms_per_launch"] * ours[k]["launches"]) if ours else None
     roof = None
     if dom:
