@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 
 #include "wfp_debug.h"
@@ -277,14 +278,17 @@ static inline unsigned nblk_u(int64_t n, int b) { return (unsigned)((n + b - 1) 
 template <typename T, int CH, int S, int WARPS>
 static void bulk_one(const Plan& pl, cudaStream_t st) {
     using G = LocalBulk<T, CH, S, WARPS>;
-    // persistent grid: the CTAs that fit on the device at once (found once per kernel instance)
-    static int fit = 0;
+    // persistent grid: the CTAs that fit on the device at once (found once per kernel instance;
+    // plans are built on several threads, so the cached value is atomic)
+    static std::atomic<int> fit_cache{0};
+    int fit = fit_cache.load(std::memory_order_relaxed);
     if (fit == 0) {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_local_bulk<T, CH, S, WARPS>, WARPS * 32, G::SMEM);
         fit = std::max(1, sms * std::max(per - 1, 1));  // one CTA slot per SM left to the advance stream
+        fit_cache.store(fit, std::memory_order_relaxed);
     }
     const int64_t need = (pl.Mt + WARPS - 1) / WARPS;
     k_local_bulk<T, CH, S, WARPS><<<(unsigned)std::min<int64_t>(need, fit), WARPS * 32, G::SMEM, st>>>(
