@@ -366,7 +366,7 @@ def source_hash(kernel: str = "local") -> str:
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2604_07170_gb300", "csrc")
-    files = {"local": ("wfp_local.cu", "wfp_ptx.h", "wfp_dev.h")}.get(kernel, ("wfp_step.cu", "wfp_dev.h"))
+    files = {"local": ("wfp_local_kernels.cuh", "wfp_ptx.h", "wfp_dev.h")}.get(kernel, ("wfp_step.cu", "wfp_dev.h"))
     for fn in files:
         with open(os.path.join(d, fn), "rb") as f:
             h.update(f.read())
