@@ -23,30 +23,41 @@ namespace wfp {
 // sigma(t_n) in caller order -> the window [M][NW] (slot n & (NW-1)), the linear window [M][32]
 // (shifted by one level, newest last; NW = 32 only) and the level-major history [n_hist][M] in
 // the grid precision (slot n % n_hist) read by both spreads.
+// LP = 32 sizeof(T) / 16 lanes per source (8 in FP32, 16 in FP64), each holding one 16-byte vector of
+// the source's linear window: the shift by one level takes the next lane's first element by a shuffle.
 template <typename T>
-__global__ void k_ingest(const int64_t* __restrict__ d_step, int64_t M, const double* __restrict__ sig_in,
-                         const int* __restrict__ perm, T* __restrict__ sigwin, int NW, T* __restrict__ siglin,
-                         T* __restrict__ sighist, int n_hist) {
+__global__ void __launch_bounds__(256) k_ingest(const int64_t* __restrict__ d_step, int64_t M,
+                                                const double* __restrict__ sig_in, const int* __restrict__ perm,
+                                                T* __restrict__ sigwin, int NW, T* __restrict__ siglin,
+                                                T* __restrict__ sighist, int n_hist) {
     using V = typename Vec16<T>::type;
-    constexpr int LP = 32 * sizeof(T) / 16;  // 16-byte vectors per 32-level row
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= M) return;
-    int64_t n = *d_step + 1;
-    double s = sig_in[perm[k]];
-    sigwin[k * NW + (n & (NW - 1))] = (T)s;
-    sighist[(n % n_hist) * M + k] = (T)s;
-    if (siglin) {
-        V* row = (V*)(siglin + k * 32);
-        V buf[LP];
+    constexpr int LP = 32 * sizeof(T) / 16;  // 16-byte vectors per 32-level row = lanes per source
+    constexpr int E = 16 / sizeof(T);        // elements per vector
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k = tid / LP;
+    const int c = (int)(tid % LP);
+    const bool valid = k < M;
+    const int64_t n = *d_step + 1;
+    double s = 0.0;
+    if (valid) {
+        s = sig_in[perm[k]];
+        if (c == 0) {
+            sigwin[k * NW + (n & (NW - 1))] = (T)s;
+            sighist[(n % n_hist) * M + k] = (T)s;
+        }
+    }
+    if (siglin) {  // uniform: the whole grid takes this branch or none of it
+        V v = {};
+        if (valid) v = ((const V*)(siglin + k * 32))[c];
+        const T* t = (const T*)&v;
+        const T next = __shfl_down_sync(0xffffffffu, t[0], 1, LP);  // the next vector's first element
+        if (valid) {
+            T out[E];
 #pragma unroll
-        for (int i = 0; i < LP; i++) buf[i] = row[i];
-        const T* t = (const T*)buf;
-        T out[32];
-#pragma unroll
-        for (int i = 0; i < 31; i++) out[i] = t[i + 1];
-        out[31] = (T)s;
-#pragma unroll
-        for (int i = 0; i < LP; i++) row[i] = ((const V*)out)[i];
+            for (int i = 0; i + 1 < E; i++) out[i] = t[i + 1];
+            out[E - 1] = (c == LP - 1) ? (T)s : next;
+            ((V*)(siglin + k * 32))[c] = *(const V*)out;
+        }
     }
 }
 
@@ -644,9 +655,10 @@ void prof_collect(Plan& pl) {
 template <typename T>
 static wfp_status ingest_t(Plan& pl, std::string& err) {
     ProfScope ps0(pl, PP_INGEST);
-    k_ingest<T><<<nblk(pl.M, 256), 256, 0, pl.stream>>>(pl.d_step, pl.M, pl.d_sig_in, pl.d_src_perm,
-                                                          (T*)pl.d_sigwin, pl.NW, (T*)pl.d_siglin, (T*)pl.d_sighist,
-                                                          pl.n_hist);
+    constexpr int LP = 32 * sizeof(T) / 16;  // lanes per source
+    k_ingest<T><<<nblk(pl.M * LP, 256), 256, 0, pl.stream>>>(pl.d_step, pl.M, pl.d_sig_in, pl.d_src_perm,
+                                                               (T*)pl.d_sigwin, pl.NW, (T*)pl.d_siglin,
+                                                               (T*)pl.d_sighist, pl.n_hist);
     CK(cudaGetLastError());
     return WFP_OK;
 }
