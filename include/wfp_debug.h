@@ -26,6 +26,13 @@ extern "C" {
 wfp_status wfp_debug_eta(double r, double dt, int W, int p, double eps, double band_limit, int ng, double* eta);
 
 /*
+ * The same weights as plans compute them: for r >= dt from the Chebyshev table of each delay
+ * interval [k dt, (k+1) dt] (series in sqrt((k+1) dt - r), built from eta_weights at Chebyshev
+ * points), for r < dt by the direct quadrature above.  Arguments as wfp_debug_eta.
+ */
+wfp_status wfp_debug_eta_table(double r, double dt, int W, int p, double eps, double band_limit, int ng, double* eta);
+
+/*
  * Near-history FIR taps at wavenumber magnitude kappa (Lemma 4.2, Eq. hggrid), dt folded in:
  * taps[0..W) = p_m, [W..2W) = q_m, [2W..3W) = pA_m, [3W..4W) = qA_m; lagshift = A+ - delta.
  * rot = {cos(kappa dt), sin(kappa dt)/kappa, kappa sin(kappa dt)}.  taps: 4W doubles, rot: 3.

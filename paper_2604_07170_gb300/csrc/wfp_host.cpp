@@ -526,4 +526,5 @@ void fill_info(const Params& P, wfp_info& I) {
     I.precision = P.precision;
 }
 
+
 }  // namespace wfp

@@ -69,6 +69,9 @@ double d2phi_host(double t, double delta, double b);               // phi''
 constexpr int kLsIntervals = 4;  // newest delay intervals interpolated by band-limited least squares
 constexpr int kLsDeg = 28;       // Chebyshev degree of the least-squares weights over those intervals
 void build_ls_cheb(int nmax, double dt, double Omega, double span, std::vector<double>& C);
+// Chebyshev table of the local weights on the delay intervals k = 1..W-1 (see eta_from_table)
+void build_eta_table(double dt, int W, int p, int nmax, const double* phicoef, const double* gx, const double* gw,
+                     int ng, const double* wl, const double* Cls, std::vector<double>& tab);
 void build_ls_cheb_into(int nmax, double dt, double Omega, double span, double* C);  // no heap use
 // W, p, nmax and eps of the local part from dt, K0 (band limit) and tol (no heap use)
 wfp_status local_params(double dt, double K0, double tol, const wfp_opts& o, double* eps, int* W, int* p, int* nmax,

@@ -90,19 +90,65 @@ __global__ void k_nbr(int pass, int64_t Mt, const double2* __restrict__ tgt, con
 }
 
 // ------------------------------------------------------------------- local weights
+// weights of each pair slot: from the per-interval Chebyshev table for r >= dt, by the direct
+// quadrature below (and for the zero-weight padding slots, r = 0)
 template <typename TW>
 __global__ void __launch_bounds__(128) k_eta(int64_t npairs, const double* __restrict__ rr, double dt, int W, int p,
                                              int nmax, int NW, const double* __restrict__ phicoef,
                                              const double* __restrict__ gx, const double* __restrict__ gw, int ng,
                                              const double* __restrict__ wl, const double* __restrict__ Cls,
-                                             TW* __restrict__ eta) {
+                                             const double* __restrict__ tab, TW* __restrict__ eta) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= npairs) return;
     double e[kMaxLevels];
-    eta_weights(rr[k], dt, W, p, nmax, phicoef, gx, gw, ng, wl, Cls, e);
+    const double r = rr[k];
+    if (tab && r >= dt && r < W * dt)
+        eta_from_table(r, dt, W, nmax, tab, e);
+    else
+        eta_weights(r, dt, W, p, nmax, phicoef, gx, gw, ng, wl, Cls, e);
     // with NW = 32 the row is aligned with the linear window (position NW - nmax + l holds level l)
     const int off = (NW == 32) ? NW - nmax : 0;
     for (int i = 0; i < NW; i++) eta[k * NW + i] = (i >= off && i - off < nmax) ? (TW)e[i - off] : (TW)0;
+}
+
+// direct weights at the table's Chebyshev nodes: out[i][l], FP64
+__global__ void k_eta_nodes(int nn, const double* __restrict__ rn, double dt, int W, int p, int nmax,
+                            const double* __restrict__ phicoef, const double* __restrict__ gx,
+                            const double* __restrict__ gw, int ng, const double* __restrict__ wl,
+                            const double* __restrict__ Cls, double* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    double e[kMaxLevels];
+    eta_weights(rn[i], dt, W, p, nmax, phicoef, gx, gw, ng, wl, Cls, e);
+    for (int l = 0; l < nmax; l++) out[(size_t)i * nmax + l] = e[l];
+}
+
+// Chebyshev coefficients of the table from the node values (host)
+static void eta_table_coefficients(int W, int nmax, const std::vector<double>& vals, std::vector<double>& tab) {
+    const int N = kEtaChebDeg + 1;
+    tab.assign((size_t)std::max(W - 1, 0) * nmax * N, 0.0);
+    for (int k = 1; k < W; k++)
+        for (int l = 0; l < nmax; l++)
+            for (int d = 0; d < N; d++) {
+                double c = 0.0;
+                for (int j = 0; j < N; j++)
+                    c += vals[((size_t)(k - 1) * N + j) * nmax + l] * std::cos(kPi * d * (j + 0.5) / N);
+                tab[((size_t)(k - 1) * nmax + l) * N + d] = (d == 0 ? 1.0 : 2.0) * c / N;
+            }
+}
+
+void build_eta_table(double dt, int W, int p, int nmax, const double* phicoef, const double* gx, const double* gw,
+                     int ng, const double* wl, const double* Cls, std::vector<double>& tab) {
+    const int N = kEtaChebDeg + 1;
+    std::vector<double> vals((size_t)std::max(W - 1, 0) * N * nmax);
+    double e[kMaxLevels];
+    for (int k = 1; k < W; k++)
+        for (int j = 0; j < N; j++) {  // Chebyshev points of the first kind in v on [0, sqrt(dt)]
+            const double v = 0.5 * (std::cos(kPi * (j + 0.5) / N) + 1.0) * std::sqrt(dt);
+            eta_weights((k + 1) * dt - v * v, dt, W, p, nmax, phicoef, gx, gw, ng, wl, Cls, e);
+            for (int l = 0; l < nmax; l++) vals[((size_t)(k - 1) * N + j) * nmax + l] = e[l];
+        }
+    eta_table_coefficients(W, nmax, vals, tab);
 }
 
 // ------------------------------------------------------------------- FIR taps
@@ -356,11 +402,31 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         T* eta = nullptr;
         CK(mem.alloc(&eta, (size_t)pl.n_slots * pl.NW));
         pl.d_eta = eta;
+        const double* Cls = pl.opts.local_interp == WFP_INTERP_LAGRANGE ? nullptr : d_bls.p;
+        // Chebyshev table of the weights on the delay intervals k >= 1: direct weights at the nodes
+        // (device), coefficients (host); pairs then evaluate the table instead of the quadrature
+        Tmp<double> d_tab;
+        if (P.W >= 2) {
+            const int N = kEtaChebDeg + 1, nn = (P.W - 1) * N;
+            std::vector<double> rn(nn), vals((size_t)nn * P.nmax), tab;
+            for (int k = 1; k < P.W; k++)
+                for (int j = 0; j < N; j++) {
+                    const double v = 0.5 * (std::cos(kPi * (j + 0.5) / N) + 1.0) * std::sqrt(P.dt);
+                    rn[(size_t)(k - 1) * N + j] = (k + 1) * P.dt - v * v;
+                }
+            Tmp<double> d_rn, d_vals;
+            CK(upload_tmp(d_rn, rn));
+            CK(d_vals.alloc(vals.size()));
+            k_eta_nodes<<<nblk(nn, 64), 64>>>(nn, d_rn.p, P.dt, P.W, P.p, P.nmax, pl.d_phicoef, d_gx.p, d_gw.p, ng,
+                                             d_wl.p, Cls, d_vals.p);
+            CK(cudaGetLastError());
+            CK(cudaMemcpy(vals.data(), d_vals.p, vals.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            eta_table_coefficients(P.W, P.nmax, vals, tab);
+            CK(upload_tmp(d_tab, tab));
+        }
         if (pl.n_slots > 0) {
             k_eta<T><<<nblk(pl.n_slots, 128), 128>>>(pl.n_slots, d_r.p, P.dt, P.W, P.p, P.nmax, pl.NW, pl.d_phicoef,
-                                                     d_gx.p, d_gw.p, ng, d_wl.p,
-                                                     pl.opts.local_interp == WFP_INTERP_LAGRANGE ? nullptr : d_bls.p,
-                                                     eta);
+                                                     d_gx.p, d_gw.p, ng, d_wl.p, Cls, d_tab.p, eta);
             CK(cudaGetLastError());
         }
         CK(cudaStreamSynchronize(cudaStreamPerThread));

@@ -107,6 +107,32 @@ WFP_HD inline void eta_weights(double r, double dt, int W, int p, int nmax, cons
 }
 
 // sin(k x)/k, continuous at k = 0
+// Chebyshev table of the local weights.  On each delay interval r in [k dt, (k+1) dt], k >= 1, the
+// weights are analytic in v = sqrt((k+1) dt - r) (the square-root behaviour where a quadrature
+// sub-interval opens at r = (k+1) dt is absorbed by the variable), so a degree-kEtaChebDeg
+// Chebyshev series in v per interval and level replaces the per-pair quadrature; r < dt (a
+// logarithmic singularity at r = 0) keeps eta_weights.  tab[((k - 1) * nmax + l) * (D + 1) + d].
+constexpr int kEtaChebDeg = 32;
+
+WFP_HD inline void eta_from_table(double r, double dt, int W, int nmax, const double* tab, double* eta) {
+    constexpr int N = kEtaChebDeg + 1;
+    int k = (int)floor(r / dt);
+    k = k < 1 ? 1 : (k > W - 1 ? W - 1 : k);
+    const double v = sqrt(fmax(0.0, (k + 1) * dt - r));
+    const double x = 2.0 * v / sqrt(dt) - 1.0;
+    const double* t = tab + (size_t)(k - 1) * nmax * N;
+    for (int l = 0; l < nmax; l++) {
+        const double* c = t + (size_t)l * N;
+        double b1 = 0.0, b2 = 0.0;
+        for (int d = N - 1; d >= 1; d--) {
+            const double b0 = fma(2.0 * x, b1, c[d] - b2);
+            b2 = b1;
+            b1 = b0;
+        }
+        eta[l] = fma(x, b1, c[0] - b2);
+    }
+}
+
 WFP_HD inline double sin_over(double k, double x) {
     double a = k * x;
     if (fabs(a) < 1e-3) {

@@ -52,7 +52,7 @@ class wfp_info(ctypes.Structure):
 _lib = None
 
 # every symbol declared in include/wfp.h and include/wfp_debug.h
-EXPORTS = ["wfp_opts_default", "wfp_plan_create", "wfp_step", "wfp_destroy", "wfp_plan_get_info",
+EXPORTS = ["wfp_debug_eta_table", "wfp_opts_default", "wfp_plan_create", "wfp_step", "wfp_destroy", "wfp_plan_get_info",
            "wfp_step_components", "wfp_select_params", "wfp_status_string", "wfp_last_error",
            "wfp_profile", "wfp_profile_read", "wfp_local_noalloc", "wfp_debug_eta", "wfp_debug_taps", "wfp_debug_phi",
            "wfp_debug_soe", "wfp_debug_hankel", "wfp_debug_bounded_wait", "wfp_checkpoint_size",
@@ -105,6 +105,8 @@ def lib():
     L.wfp_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), _pd,
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]
     L.wfp_debug_eta.argtypes = [_c_dbl, _c_dbl, ctypes.c_int, ctypes.c_int, _c_dbl, _c_dbl, ctypes.c_int, _pd]
+    L.wfp_debug_eta_table.argtypes = [_c_dbl, _c_dbl, ctypes.c_int, ctypes.c_int, _c_dbl, _c_dbl, ctypes.c_int, _pd]
+    L.wfp_debug_eta_table.restype = ctypes.c_int
     L.wfp_debug_taps.argtypes = [_c_dbl, _c_dbl, ctypes.c_int, _c_dbl, _c_dbl, _pd, _pd]
     L.wfp_debug_phi.argtypes = [_c_dbl, _c_dbl, _c_dbl, _pd, _pd, _pd]
     L.wfp_debug_soe.argtypes = [_c_dbl, ctypes.c_int, ctypes.c_int, _pd, _pd]
@@ -335,6 +337,12 @@ class Server:
 def debug_eta(r, dt, W, p=20, eps=1e-8, band_limit=0.0, ng=20) -> np.ndarray:
     out = np.zeros(W + 1 + p // 2)
     _check(lib().wfp_debug_eta(r, dt, W, p, eps, band_limit, ng, _dptr(out)), "wfp_debug_eta")
+    return out
+
+
+def debug_eta_table(r, dt, W, p=20, eps=1e-8, band_limit=0.0, ng=20) -> np.ndarray:
+    out = np.zeros(W + 1 + p // 2)
+    _check(lib().wfp_debug_eta_table(r, dt, W, p, eps, band_limit, ng, _dptr(out)), "wfp_debug_eta_table")
     return out
 
 

@@ -237,3 +237,16 @@ def test_fixed_delta_sets_W_and_bounds_are_checked():
         wfp.select_params(10.0, 0.1, 400, 12.7, 1e-6, delta=0.3)  # W = 3 violates Eq. dt
     with pytest.raises(wfp.WFPError):
         wfp.select_params(10.0, 0.1, 400, 12.7, 1e-6, local_interp=5)
+
+
+def test_local_weight_table_matches_the_quadrature():
+    # plans evaluate the local weights from a Chebyshev series per delay interval (in sqrt of the
+    # distance to the interval's end); it must reproduce the direct quadrature to rounding
+    rng = np.random.default_rng(3)
+    for dt, W, p, eps, K0 in ((0.0077, 23, 16, 1e-9, 165.4), (0.02, 24, 12, 1e-8, -1.0)):
+        worst = 0.0
+        for r in np.concatenate([rng.uniform(dt, W * dt, 6), [dt * (1 + 1e-12), 2 * dt, (W - 1) * dt, W * dt * (1 - 1e-9)]]):
+            a = wfp.debug_eta(r, dt, W, p, eps, K0)
+            b = wfp.debug_eta_table(r, dt, W, p, eps, K0)
+            worst = max(worst, float(np.max(np.abs(a - b))))
+        assert worst <= 1e-13, (dt, W, worst)
