@@ -165,7 +165,18 @@ def part_model(info: dict, M: int, Mt: int, fp64: bool) -> dict:
     spreads = 1 + (lag and not info["lag_store"])  # a second (lagged) spread only without the stored S history
     tapw = 4 * W * s if fp64 else 8 * W * 4     # FIR taps per |k|: FP64, or FP32 hi/lo pairs
     m = {}
-    m["local"] = (npair * (NW * s + 4) + M * NW * s + Mt * (8 + 8), 2 * npair * info["nmax"])
+    if info.get("local_form") == 2:
+        # factored form: pair records (8 bytes, 16 in FP64), near pairs' stored rows, the per-step
+        # contraction y written once and read once, the windows, row pointers and the output;
+        # flops: the contraction (2 * 32 * NC per source and interval) and per table pair the
+        # Chebyshev recurrence and dot product (2 * (2 NC - 2)), per near pair a 32-level dot product
+        nc, nnear = info["local_nc"], info["n_near_pairs"]
+        ntab = npair - nnear
+        ybytes = (W - 1) * M * nc * s
+        m["local"] = (ntab * 2 * s + nnear * (NW * s + 4) + 2 * ybytes + M * NW * s + Mt * (16 + 8),
+                      2 * 32 * nc * (W - 1) * M + ntab * 2 * (2 * nc - 2) + nnear * 2 * NW)
+    else:
+        m["local"] = (npair * (NW * s + 4) + M * NW * s + Mt * (8 + 8), 2 * npair * info["nmax"])
     # shared window (W levels) + one-tap recurrences: Z_l read and written, FP64
     m["self"] = (nself * (nsoe * 16 + W * s + 12), nself * (nsoe * 4 + 2 * W))
     m["ingest"] = (M * (8 + 4 + 2 * s + (2 * NW * s if NW == 32 else 0)), 0)
@@ -329,10 +340,14 @@ def roofline(r: dict, M: int, Mt: int, fp64: bool) -> tuple[dict, dict]:
             with open(tj) as f:
                 tr = json.load(f)
             key = f"{dom}:{'fp64' if fp64 else 'mixed'}:{r['workload']}"
-            if dom == "local":  # per variant (the autotuner may pick any of the bit-identical forms)
+            hkind = dom
+            if dom == "local" and r["info"].get("local_form") == 2:
+                key += ":factored"
+                hkind = "local_factored"
+            elif dom == "local":  # per variant (the autotuner may pick any of the bit-identical forms)
                 key += f":v{r['info'].get('local_variant')}"
             ent = tr.get(key, {})
-            if ent.get("source_hash") == source_hash(dom):
+            if ent.get("source_hash") == source_hash(hkind):
                 traffic = ent["bytes_per_launch"]
         if e["bound"] == "hbm":
             roof = {"kernel": dom, "bound": "hbm", "achieved": round(e["GB/s"], 1), "peak": peaks["hbm_gbs"],
@@ -368,7 +383,9 @@ def source_hash(kernel: str = "local") -> str:
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2604_07170_gb300", "csrc")
-    files = {"local": ("wfp_local_kernels.cuh", "wfp_ptx.h", "wfp_dev.h")}.get(kernel, ("wfp_step.cu", "wfp_dev.h"))
+    files = {"local": ("wfp_local_kernels.cuh", "wfp_ptx.h", "wfp_dev.h"),
+             "local_factored": ("wfp_local_factored.cuh", "wfp_local_kernels.cuh", "wfp_dev.h")}.get(
+        kernel, ("wfp_step.cu", "wfp_dev.h"))
     for fn in files:
         with open(os.path.join(d, fn), "rb") as f:
             h.update(f.read())
@@ -377,9 +394,11 @@ def source_hash(kernel: str = "local") -> str:
 
 def launches_per_step(info: dict, n_self: int) -> int:
     """Kernels of this library per step in the lagged regime (cuFFT's own kernels not counted):
-    ingest, local, [self], combine, spread (x2 when the lag is recomputed), modes, [far], interp, tick."""
+    ingest, local (two in the factored form), [self], combine, spread (x2 when the lag is recomputed),
+    modes, [far], interp, tick."""
     spreads = 1 if info["lag_store"] else 2
-    return 1 + 1 + (1 if n_self > 0 else 0) + 1 + spreads + 1 + (1 if info["far_active"] else 0) + 1 + 1
+    local = 2 if info.get("local_form") == 2 else 1
+    return 1 + local + (1 if n_self > 0 else 0) + 1 + spreads + 1 + (1 if info["far_active"] else 0) + 1 + 1
 
 
 def drive(args):

@@ -92,6 +92,18 @@ enum { WFP_FP64 = 0, WFP_MIXED = 1 };
  *                 (0, default) fits the newest four intervals by band-limited least squares and uses
  *                 p-point Lagrange elsewhere; WFP_INTERP_LAGRANGE uses p-point Lagrange on the p nearest
  *                 grid values everywhere, as the paper does (order-p convergence, Sec. 7).
+ *   local_form    how the local weights eta_l(r_ij) of Sec. 6 reach the step.  WFP_LOCAL_STORED: one
+ *                 row of nmax weights per pair, computed at plan time and streamed from device memory
+ *                 every step.  WFP_LOCAL_FACTORED: on each delay interval [k dt, (k+1) dt], k >= 1, the
+ *                 weights are a Chebyshev series in v = sqrt((k+1) dt - r); the step first contracts
+ *                 each source's signal window with the series coefficients (y_{j,k,c}, per source,
+ *                 interval and coefficient) and each pair then sums T_c(v_ij) y_{j,k,c} -- the same
+ *                 weights, factored, with a pair costing 8 bytes (16 in FP64) instead of a weight row;
+ *                 pairs with r < dt keep stored rows.  The series is cut after the first coefficient
+ *                 count (a multiple of 4) whose dropped tail is below the path's rounding (below 2^-25
+ *                 of the interval's weight scale on the MIXED path; every coefficient on the FP64 path).
+ *                 WFP_LOCAL_AUTO (0, default): FACTORED on the MIXED path, STORED on the FP64 path (where
+ *                 the stored form needs fewer FP64 operations per pair).  FACTORED needs nmax <= 32.
  */
 typedef struct {
     int precision;
@@ -111,9 +123,12 @@ typedef struct {
     int local_variant;
     int local_interp;
     double delta;
+    int local_form;
 } wfp_opts;
 
 enum { WFP_INTERP_HYBRID = 0, WFP_INTERP_LAGRANGE = 1 };
+
+enum { WFP_LOCAL_AUTO = 0, WFP_LOCAL_STORED = 1, WFP_LOCAL_FACTORED = 2 };
 
 enum { WFP_LAG_AUTO = 0, WFP_LAG_RECOMPUTE = 1, WFP_LAG_STORE = 2 };
 
@@ -144,7 +159,11 @@ typedef struct {
     int lag_store;                   /* 1: S history stored (L + W levels), 0: lagged NUFFT */
     int64_t s_levels;                /* levels of S kept per mode */
     int spread_tile, spread_chunk;   /* spreading tile side and staging chunk in use */
-    int local_variant;               /* local-part kernel variant in use (0: 64-level window form) */
+    int local_variant;               /* local-part kernel variant in use (0: 64-level window form
+                                        or the factored form) */
+    int local_form;                  /* WFP_LOCAL_STORED or WFP_LOCAL_FACTORED, as built */
+    int local_nc;                    /* Chebyshev coefficients per interval (factored form), else 0 */
+    int64_t n_near_pairs;            /* pairs with r < dt (stored weight rows in the factored form) */
 } wfp_info;
 
 typedef struct wfp_plan_s* wfp_plan;

@@ -320,7 +320,10 @@ wfp_status wfp_plan_get_info(wfp_plan plan, wfp_info* info) {
     info->s_levels = pl.R_cur;
     info->spread_tile = pl.spread_ts;
     info->spread_chunk = pl.spread_ch;
-    info->local_variant = pl.NW == 32 ? pl.local_variant : 0;
+    info->local_variant = (pl.NW == 32 && !pl.local_factored) ? pl.local_variant : 0;
+    info->local_form = pl.local_factored ? WFP_LOCAL_FACTORED : WFP_LOCAL_STORED;
+    info->local_nc = pl.local_factored ? pl.NC : 0;
+    info->n_near_pairs = pl.local_factored ? pl.n_near : 0;
     return WFP_OK;
 }
 

@@ -392,6 +392,10 @@ wfp_status select_params(double halfside, double dt, int64_t Nt, double K0, doub
         err = "local_interp must be WFP_INTERP_HYBRID or WFP_INTERP_LAGRANGE";
         return WFP_EINVAL;
     }
+    if (o.local_form < WFP_LOCAL_AUTO || o.local_form > WFP_LOCAL_FACTORED) {
+        err = "local_form must be WFP_LOCAL_AUTO, WFP_LOCAL_STORED or WFP_LOCAL_FACTORED";
+        return WFP_EINVAL;
+    }
     P.precision = o.precision;
     P.exclude_self = o.exclude_self != 0;
     P.scale = 1.0 / halfside;

@@ -11,6 +11,7 @@
 
 #include "wfp_debug.h"
 #include "wfp_dev.h"
+#include "wfp_local_factored.cuh"
 #include "wfp_local_kernels.cuh"
 #include "wfp_plan.h"
 #include "wfp_ptx.h"
@@ -82,10 +83,48 @@ void local_launch(const Plan& pl, int variant, cudaStream_t st) {
         local_variant_t<float>(pl, variant, st);
 }
 
-// Local part of the current step into pl.d_uloc (64-level windows use k_local; otherwise the
-// variant chosen at plan time).
+// Factored form: the per-step contraction of the windows, then the pair sums.
+template <typename T, int NC>
+static void factored_nc(const Plan& pl, cudaStream_t st) {
+    const int nk = pl.P.W - 1;
+    if constexpr (sizeof(T) == 8) {
+        k_ycoef<T, NC><<<dim3(nblk_u(pl.M, 128), (unsigned)nk), 128, 0, st>>>(pl.M, (const T*)pl.d_siglin,
+                                                                            (const T*)pl.d_ctab, (T*)pl.d_ycoef);
+        k_local_cheb<T, NC><<<nblk_u(pl.Mt * 32, 256), 256, 0, st>>>(
+            pl.Mt, pl.M, pl.d_trow, (const TabPair<T>*)pl.d_tpair, (const T*)pl.d_ycoef, pl.d_rowptr, pl.d_col,
+            (const T*)pl.d_eta, (const T*)pl.d_siglin, pl.d_uloc);
+    } else {
+        constexpr int KC = 64 / NC;  // intervals per block of k_ycoef4
+        k_ycoef4<NC><<<dim3(nblk_u(pl.M, 32), (unsigned)((nk + KC - 1) / KC)), 128, 0, st>>>(
+            pl.M, nk, (const float*)pl.d_siglin, (const float*)pl.d_ctab, (float*)pl.d_ycoef);
+        k_local_cheb4<NC><<<nblk_u(pl.Mt * 32, 256), 256, 0, st>>>(
+            pl.Mt, pl.M, pl.d_trow, (const TabPair<float>*)pl.d_tpair, (const float*)pl.d_ycoef, pl.d_rowptr,
+            pl.d_col, (const float*)pl.d_eta, (const float*)pl.d_siglin, pl.d_uloc);
+    }
+}
+
+static void factored_run(const Plan& pl, cudaStream_t st) {
+    if (pl.P.precision == WFP_FP64)
+        factored_nc<double, 36>(pl, st);
+    else if (pl.NC == 16)
+        factored_nc<float, 16>(pl, st);
+    else
+        factored_nc<float, 32>(pl, st);
+}
+
+// coefficient counts the factored kernels are built for: all 33 (padded to 36) in FP64; blocks of
+// 16 or 32 in FP32
+int factored_nc_supported(int nc, bool fp64) {
+    if (fp64) return 36;
+    return nc <= 16 ? 16 : 32;
+}
+
+// Local part of the current step into pl.d_uloc (the factored form; or, with stored weight rows,
+// k_local for 64-level windows and otherwise the variant chosen at plan time).
 void local_run(const Plan& pl, cudaStream_t st) {
-    if (pl.NW == 32) {
+    if (pl.local_factored) {
+        factored_run(pl, st);
+    } else if (pl.NW == 32) {
         local_launch(pl, pl.local_variant, st);
     } else if (pl.P.precision == WFP_FP64) {
         k_local<double><<<nblk_u(pl.Mt * 32, 256), 256, 0, st>>>(pl.d_step, pl.Mt, pl.d_rowptr, pl.d_col,

@@ -1,0 +1,332 @@
+// Factored local part of the 2D TK-WFP step (Sec. 6, Eq. ul) on sm_103a; launched from
+// wfp_local.cu.  The pair records are also written at plan time (wfp_plan.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "wfp_dev.h"
+#include "wfp_local_kernels.cuh"  // kahan_add
+
+namespace wfp {
+
+// One pair of the factored local part: source index j and delay-interval index k - 1 packed as
+// j | (k - 1) << 26, and the interval's Chebyshev variable x = 2 sqrt(((k+1) dt - r) / dt) - 1.
+template <typename T>
+struct TabPair;
+template <>
+struct __align__(8) TabPair<float> {
+    unsigned ck;
+    float x;
+};
+template <>
+struct __align__(16) TabPair<double> {
+    unsigned ck, pad;
+    double x;
+};
+constexpr unsigned kTabPairSrcMask = (1u << 26) - 1;
+
+// ------------------------------------------------------------------ factored local part
+// On a delay interval [k dt, (k+1) dt], k >= 1, each weight is a Chebyshev series in the interval's
+// variable x(r): eta_l(r) = sum_c C[k][l][c] T_c(x(r)).  Summing over the levels first,
+//   sum_l eta_l(r_ij) sigma_j,l = sum_c T_c(x_ij) y[k][j][c],   y[k][j][c] = sum_l C[k][l][c] sigma_j,l,
+// so one contraction per source and interval per step (k_ycoef) replaces a weight row per pair, and
+// a pair needs only (j, k, x): 8 bytes instead of 32 weights.  y is small (sources x intervals x NC)
+// and gathered from L2 by the pairs.
+
+template <typename T>
+__device__ __forceinline__ void unpack16(const typename Vec16<T>::type& q, T* out);
+template <>
+__device__ __forceinline__ void unpack16<float>(const float4& q, float* out) {
+    out[0] = q.x;
+    out[1] = q.y;
+    out[2] = q.z;
+    out[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void unpack16<double>(const double2& q, double* out) {
+    out[0] = q.x;
+    out[1] = q.y;
+}
+
+// y[kk][j][c] = sum_i ctab[kk][i][c] siglin[j][i] (window position i = 32 - nmax + l holds level l;
+// the coefficients of the unused positions are zero).  Thread = source, blockIdx.y = interval; the
+// interval's coefficients are staged in shared memory and read as warp-uniform broadcasts.
+template <typename T, int NC>
+__global__ void __launch_bounds__(128) k_ycoef(int64_t M, const T* __restrict__ siglin, const T* __restrict__ ctab,
+                                               T* __restrict__ y) {
+    using V = typename Vec16<T>::type;
+    constexpr int EV = 16 / (int)sizeof(T);
+    __shared__ __align__(16) T sc[32 * NC];
+    const int kk = blockIdx.y;
+    for (int t = threadIdx.x; t < 32 * NC; t += blockDim.x) sc[t] = ctab[(int64_t)kk * 32 * NC + t];
+    __syncthreads();
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    T s[32];
+    const V* sp = (const V*)(siglin + j * 32);
+#pragma unroll
+    for (int v = 0; v < 32 / EV; v++) unpack16<T>(__ldg(sp + v), s + v * EV);
+    V* out = (V*)(y + ((int64_t)kk * M + j) * NC);
+#pragma unroll
+    for (int c0 = 0; c0 < NC; c0 += 4) {
+        T a[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < 32; i++) {
+            const T* cr = sc + i * NC + c0;
+#pragma unroll
+            for (int q = 0; q < 4; q++) a[q] = fma(cr[q], s[i], a[q]);
+        }
+        if constexpr (sizeof(T) == 4) {
+            out[c0 / 4] = make_float4(a[0], a[1], a[2], a[3]);
+        } else {
+            out[c0 / 2] = make_double2(a[0], a[1]);
+            out[c0 / 2 + 1] = make_double2(a[2], a[3]);
+        }
+    }
+}
+
+// sum_c T_c(x) yy[c], with T_c by the three-term recurrence T_{c+1} = 2x T_c - T_{c-1} (even and odd
+// terms in two partial sums)
+template <typename T, int NC>
+__device__ __forceinline__ T cheb_dot(T x, const T* yy) {
+    const T x2 = x + x;
+    T tm = 1, tc = x;
+    T s0 = yy[0], s1 = yy[1] * x;
+#pragma unroll
+    for (int c = 2; c < NC; c++) {
+        const T tn = fma(x2, tc, -tm);
+        if (c & 1)
+            s1 = fma(tn, yy[c], s1);
+        else
+            s0 = fma(tn, yy[c], s0);
+        tm = tc;
+        tc = tn;
+    }
+    return s0 + s1;
+}
+
+// streamed (read-once) load of a pair record
+__device__ __forceinline__ TabPair<float> load_pair(const TabPair<float>* p) {
+    const uint2 q = __ldcs((const uint2*)p);
+    return TabPair<float>{q.x, __uint_as_float(q.y)};
+}
+__device__ __forceinline__ TabPair<double> load_pair(const TabPair<double>* p) {
+    const double2 q = __ldcs((const double2*)p);
+    return TabPair<double>{(unsigned)(unsigned long long)__double_as_longlong(q.x), 0u, q.y};
+}
+
+template <typename T, int NC>
+__device__ __forceinline__ T tab_pair_value(const TabPair<T>& e, int64_t M, const T* __restrict__ y) {
+    using V = typename Vec16<T>::type;
+    constexpr int EV = 16 / (int)sizeof(T);
+    const int64_t j = (int64_t)(e.ck & kTabPairSrcMask), kk = (int64_t)(e.ck >> 26);
+    const V* yb = (const V*)(y + (kk * M + j) * NC);
+    T yy[NC];
+#pragma unroll
+    for (int v = 0; v < NC / EV; v++) unpack16<T>(__ldg(yb + v), yy + v * EV);
+    return cheb_dot<T, NC>(e.x, yy);
+}
+
+// FP64 form (coefficients in natural order): one warp per target row, one lane per pair (the row's
+// table pairs 32 apart), then its near pairs (r < dt, stored 32-level rows against the source's
+// window), one lane each.
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_local_cheb(int64_t Mt, int64_t M, const int64_t* __restrict__ trow,
+                                                    const TabPair<T>* __restrict__ tp, const T* __restrict__ y,
+                                                    const int64_t* __restrict__ nrow, const int* __restrict__ ncol,
+                                                    const T* __restrict__ neta, const T* __restrict__ siglin,
+                                                    double* __restrict__ uloc) {
+    using V = typename Vec16<T>::type;
+    constexpr int EV = 16 / (int)sizeof(T);
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= Mt) return;
+    float sm = 0.f, cm = 0.f;  // FP32: compensated sum
+    double d = 0.0;            // FP64
+    const int64_t p1 = trow[row + 1];
+    int64_t p = trow[row] + lane;
+    if constexpr (sizeof(T) == 4) {
+        for (; p + 32 < p1; p += 64) {
+            const TabPair<T> e0 = load_pair(tp + p), e1 = load_pair(tp + p + 32);
+            const float v0 = tab_pair_value<T, NC>(e0, M, y);
+            const float v1 = tab_pair_value<T, NC>(e1, M, y);
+            kahan_add(sm, cm, v0);
+            kahan_add(sm, cm, v1);
+        }
+        if (p < p1) kahan_add(sm, cm, tab_pair_value<T, NC>(load_pair(tp + p), M, y));
+    } else {
+        for (; p < p1; p += 32) d += tab_pair_value<T, NC>(load_pair(tp + p), M, y);
+    }
+    for (int64_t q = nrow[row] + lane; q < nrow[row + 1]; q += 32) {
+        const V* E = (const V*)(neta + q * 32);
+        const V* X = (const V*)(siglin + (int64_t)ncol[q] * 32);
+        T a0 = 0, a1 = 0;
+#pragma unroll
+        for (int v = 0; v < 32 / EV; v++) {
+            T e[EV], x[EV];
+            unpack16<T>(__ldcs(E + v), e);
+            unpack16<T>(__ldg(X + v), x);
+#pragma unroll
+            for (int u = 0; u < EV; u += 2) {
+                a0 = fma(e[u], x[u], a0);
+                a1 = fma(e[u + 1], x[u + 1], a1);
+            }
+        }
+        if constexpr (sizeof(T) == 4)
+            kahan_add(sm, cm, a0 + a1);
+        else
+            d += a0 + a1;
+    }
+    double tot = (sizeof(T) == 4) ? (double)sm - (double)cm : d;
+    tot = warp_sum(tot);
+    if (lane == 0) uloc[row] = tot;
+}
+
+
+// FP32 form.  A pair's y block (NC = 16 or 32 floats, 64 or 128 contiguous bytes) is read by four
+// lanes, 16 bytes each per load, so one warp load gathers eight whole blocks (eight L1 wavefronts)
+// instead of 32 scattered 16-byte pieces.  The block is stored lane-interleaved by coefficient
+// residue: position 16 v + 4 q + e holds c = q + 4 (4 v + e), so lane q holds T_q, T_{q+4}, ... and
+// runs the stride-4 recurrence T_{c+4} = 2 T_4 T_c - T_{c-4} (with T_{q-4} = T_{4-q}).
+template <int NV>
+__device__ __forceinline__ float cheb_quarter(float x, const float* yy, int q) {
+    const float x2 = x + x;
+    const float t2 = fmaf(x2, x, -1.f), t3 = fmaf(x2, t2, -x), t4 = fmaf(x2, t3, -t2);
+    float a = q == 0 ? 1.f : (q == 1 ? x : (q == 2 ? t2 : t3));  // T_q
+    float b = q == 0 ? t4 : (q == 1 ? t3 : (q == 2 ? t2 : x));   // T_{q-4} = T_{4-q}
+    const float w4 = t4 + t4;
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int m = 0; m < 4 * NV; m++) {
+        if (m & 1)
+            s1 = fmaf(a, yy[m], s1);
+        else
+            s0 = fmaf(a, yy[m], s0);
+        const float n = fmaf(w4, a, -b);
+        b = a;
+        a = n;
+    }
+    return s0 + s1;
+}
+
+// One warp per target row; lanes (g, q) = (lane / 4, lane % 4) take the row's table pairs 8 apart,
+// four per lane in flight (their records, then their blocks, loaded before any is used; the four
+// values are added, then compensated into the lane's FP32 sum).  Near pairs (r < dt): eight lanes
+// per stored row, one 16-byte vector each.  The 32 lanes' sums are added in FP64 at the end.  Block
+// indices are 32-bit (the plan keeps (W - 1) M NC / 4 below 2^32).
+template <int NC>
+__global__ void __launch_bounds__(256) k_local_cheb4(int64_t Mt, int64_t M, const int64_t* __restrict__ trow,
+                                                     const TabPair<float>* __restrict__ tp, const float* __restrict__ y,
+                                                     const int64_t* __restrict__ nrow, const int* __restrict__ ncol,
+                                                     const float* __restrict__ neta, const float* __restrict__ siglin,
+                                                     double* __restrict__ uloc) {
+    static_assert(NC == 16 || NC == 32, "blocks of 16 or 32 coefficients");
+    constexpr int NV = NC / 16;  // 16-byte loads per lane per pair
+    constexpr int U = 4;
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= Mt) return;
+    const int q = lane & 3, g = lane >> 2;
+    const uint32_t Mu = (uint32_t)M;
+    float sm = 0.f, cm = 0.f;
+    const float4* Y = (const float4*)y;
+    const int64_t p1 = trow[row + 1];
+    int64_t p = trow[row] + g;
+    for (; p + 8 * (U - 1) < p1; p += 8 * U) {
+        TabPair<float> e[U];
+        float yy[U][4 * NV];
+#pragma unroll
+        for (int u = 0; u < U; u++) e[u] = load_pair(tp + p + 8 * u);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t blk = (e[u].ck >> 26) * Mu + (e[u].ck & kTabPairSrcMask);
+#pragma unroll
+            for (int v = 0; v < NV; v++) unpack16<float>(__ldg(Y + (blk * (4 * NV) + 4 * v + q)), yy[u] + 4 * v);
+        }
+        float acc = 0.f;
+#pragma unroll
+        for (int u = 0; u < U; u++) acc += cheb_quarter<NV>(e[u].x, yy[u], q);
+        kahan_add(sm, cm, acc);
+    }
+    for (; p < p1; p += 8) {
+        const TabPair<float> e = load_pair(tp + p);
+        const uint32_t blk = (e.ck >> 26) * Mu + (e.ck & kTabPairSrcMask);
+        float yy[4 * NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) unpack16<float>(__ldg(Y + (blk * (4 * NV) + 4 * v + q)), yy + 4 * v);
+        kahan_add(sm, cm, cheb_quarter<NV>(e.x, yy, q));
+    }
+    const int c8 = lane & 7, g8 = lane >> 3;
+    const float4* E = (const float4*)neta;
+    const float4* X = (const float4*)siglin;
+    for (int64_t r = nrow[row] + g8; r < nrow[row + 1]; r += 4) {
+        const float4 ev = __ldcs(E + r * 8 + c8), xv = __ldg(X + (int64_t)ncol[r] * 8 + c8);
+        kahan_add(sm, cm, fmaf(ev.w, xv.w, fmaf(ev.z, xv.z, fmaf(ev.y, xv.y, ev.x * xv.x))));
+    }
+    double tot = (double)sm - (double)cm;
+    tot = warp_sum(tot);
+    if (lane == 0) uloc[row] = tot;
+}
+
+// FP32 contraction as a register-blocked product of two shared-memory tiles: the windows of 32
+// sources (transposed, [level][source]) times the coefficients of KC = 64 / NC intervals
+// ([level][interval, position]).  Thread (a, b) accumulates sources 4a..4a+3 x positions
+// 4b..4b+3: per level two 16-byte shared loads feed 16 FMAs.  Tiles are filled by coalesced loads.
+template <int NC>
+__global__ void __launch_bounds__(128) k_ycoef4(int64_t M, int nk, const float* __restrict__ siglin,
+                                                const float* __restrict__ ctab, float* __restrict__ y) {
+    constexpr int KC = 64 / NC, QN = NC / 4;
+    __shared__ __align__(16) float sT[32][36];  // [level][source], rows padded
+    __shared__ __align__(16) float sc[32][64];  // [level][(interval - k0) * NC + position]
+    const int64_t j0 = (int64_t)blockIdx.x * 32;
+    const int k0 = blockIdx.y * KC, nkc = min(nk - k0, KC);
+    for (int t = threadIdx.x; t < 32 * 8; t += 128) {  // 32 windows of 8 vectors
+        const int s = t >> 3, v = t & 7;
+        const float4 z = (j0 + s < M) ? __ldg((const float4*)(siglin + (j0 + s) * 32) + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+        sT[4 * v][s] = z.x;
+        sT[4 * v + 1][s] = z.y;
+        sT[4 * v + 2][s] = z.z;
+        sT[4 * v + 3][s] = z.w;
+    }
+    const float4* C4 = (const float4*)(ctab + (int64_t)k0 * 32 * NC);
+    for (int t = threadIdx.x; t < KC * 32 * QN; t += 128) {  // [interval][level][position / 4]
+        const int kl = t / (32 * QN), i = (t / QN) % 32, qq = t % QN;
+        *(float4*)&sc[i][kl * NC + 4 * qq] = (kl < nkc) ? __ldg(C4 + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    const int b = threadIdx.x & 15, a = threadIdx.x >> 4;
+    float acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int e = 0; e < 4; e++) acc[r][e] = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < 32; i++) {
+        const float4 sa = *(const float4*)&sT[i][4 * a];
+        const float4 cb = *(const float4*)&sc[i][4 * b];
+        const float sv[4] = {sa.x, sa.y, sa.z, sa.w}, cv[4] = {cb.x, cb.y, cb.z, cb.w};
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int e = 0; e < 4; e++) acc[r][e] = fmaf(sv[r], cv[e], acc[r][e]);
+    }
+    const int kk = k0 + (4 * b) / NC, qq = ((4 * b) % NC) / 4;
+    if (kk >= nk) return;
+    float4* Y4 = (float4*)y;
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int64_t j = j0 + 4 * a + r;
+        if (j < M) Y4[((int64_t)kk * M + j) * QN + qq] = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+    }
+}
+
+// position of coefficient c in an FP32 block of NC (16 or 32): the inverse of c = q + 4 (4 v + e)
+// at position 16 v + 4 q + e
+__host__ __device__ inline int cheb4_position(int c) {
+    const int q = c & 3, m = c >> 2;
+    return 16 * (m >> 2) + 4 * q + (m & 3);
+}
+
+}  // namespace wfp

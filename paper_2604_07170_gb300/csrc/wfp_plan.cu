@@ -13,6 +13,7 @@
 #include <numeric>
 #include <vector>
 
+#include "wfp_local_factored.cuh"
 #include "wfp_plan.h"
 #include "wfp_quad.h"
 
@@ -149,6 +150,76 @@ void build_eta_table(double dt, int W, int p, int nmax, const double* phicoef, c
             for (int l = 0; l < nmax; l++) vals[((size_t)(k - 1) * N + j) * nmax + l] = e[l];
         }
     eta_table_coefficients(W, nmax, vals, tab);
+}
+
+// Factored form: split the pairs of each target row by delay interval -- r >= dt to the table
+// pairs (interval k = floor(r / dt) and its Chebyshev variable, exactly as eta_from_table forms
+// them), r < dt to the near pairs that keep stored weight rows; row order is kept.  Pass 0 counts,
+// pass 1 writes.
+template <typename T>
+__global__ void k_split(int pass, int64_t Mt, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                        const double* __restrict__ rr, double dt, int W, int* __restrict__ ntab,
+                        int* __restrict__ nnear, const int64_t* __restrict__ trow, const int64_t* __restrict__ nrow,
+                        TabPair<T>* __restrict__ tp, int* __restrict__ ncol, double* __restrict__ nr) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Mt) return;
+    const int64_t a = pass ? trow[i] : 0, b = pass ? nrow[i] : 0;
+    int ca = 0, cb = 0;
+    for (int64_t s = rowptr[i]; s < rowptr[i + 1]; s++) {
+        const double r = rr[s];
+        if (!(r > 0.0)) continue;
+        if (r >= dt && r < W * dt) {
+            if (pass) {
+                int k = (int)floor(r / dt);
+                k = k < 1 ? 1 : (k > W - 1 ? W - 1 : k);
+                const double v = sqrt(fmax(0.0, (k + 1) * dt - r));
+                TabPair<T> e;
+                e.ck = (unsigned)col[s] | ((unsigned)(k - 1) << 26);
+                if constexpr (sizeof(T) == 8) e.pad = 0u;
+                e.x = (T)(2.0 * v / sqrt(dt) - 1.0);
+                tp[a + ca] = e;
+            }
+            ca++;
+        } else {
+            if (pass) {
+                ncol[b + cb] = col[s];
+                nr[b + cb] = r;
+            }
+            cb++;
+        }
+    }
+    if (!pass) {
+        ntab[i] = ca;
+        nnear[i] = cb;
+    }
+}
+
+// Coefficients to keep per interval in the factored form: the smallest multiple of 4 whose dropped
+// tail, sum_{c >= NC} |C[k][l][c]|, is at most 2^-25 of the interval's weight scale
+// max_l sum_c |C[k][l][c]| for every level and interval (reduced precision); every coefficient in
+// FP64.
+static int choose_nc(const std::vector<double>& tab, int W, int nmax, bool fp64) {
+    const int N = kEtaChebDeg + 1;
+    if (fp64 || tab.empty()) return 36;
+    const double thr = std::ldexp(1.0, -25);
+    for (int nc = 8; nc <= 32; nc += 4) {
+        bool ok = true;
+        for (int kk = 0; kk < W - 1 && ok; kk++) {
+            double scale = 0.0;
+            for (int l = 0; l < nmax; l++) {
+                double a = 0.0;
+                for (int c = 0; c < N; c++) a += std::fabs(tab[((size_t)kk * nmax + l) * N + c]);
+                scale = std::max(scale, a);
+            }
+            for (int l = 0; l < nmax && ok; l++) {
+                double tail = 0.0;
+                for (int c = nc; c < N; c++) tail += std::fabs(tab[((size_t)kk * nmax + l) * N + c]);
+                ok = tail <= thr * scale;
+            }
+        }
+        if (ok) return nc;
+    }
+    return 36;
 }
 
 // ------------------------------------------------------------------- FIR taps
@@ -330,6 +401,12 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
     CK(upload(mem, &pl.d_tgt_perm, torder));
 
     // ---- neighbour search (Sec. 6: N_delta = {j : 0 < r_ij < delta})
+    const int form = local_form_of(P, pl.opts);
+    if (form < 0) {
+        err = "local_form WFP_LOCAL_FACTORED needs nmax <= 32, W >= 2 and fewer than 2^26 sources";
+        return WFP_EUNSUPPORTED;
+    }
+    pl.local_factored = form == WFP_LOCAL_FACTORED;
     {
         Tmp<double> d_s, d_t, d_r;
         Tmp<int> d_cs, d_cnt, d_self, d_ns;
@@ -347,15 +424,17 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(cudaMemcpy(cnt.data(), d_cnt.p, Mt * sizeof(int), cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(selfj.data(), d_self.p, Mt * sizeof(int), cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(ns.data(), d_ns.p, Mt * sizeof(int), cudaMemcpyDeviceToHost));
-        // rows padded to a multiple of 4 pair slots (zero-weight slots with r = 0, source 0), so that
-        // every row starts 16-byte aligned in the index array for the bulk copies of the local part
+        // stored form: rows padded to a multiple of 4 pair slots (zero-weight slots with r = 0, source
+        // 0), so that every row starts 16-byte aligned in the index array for the bulk copies of the
+        // local part; factored form: unpadded (the pairs are split by interval below)
+        const bool fac = pl.local_factored;
         std::vector<int64_t> rowptr(Mt + 1, 0);
         pl.n_pairs = 0;
         for (int64_t i = 0; i < Mt; i++) {
-            rowptr[i + 1] = rowptr[i] + ((cnt[i] + 3) & ~3);
+            rowptr[i + 1] = rowptr[i] + (fac ? cnt[i] : ((cnt[i] + 3) & ~3));
             pl.n_pairs += cnt[i];
         }
-        pl.n_slots = rowptr[Mt];
+        const int64_t nall = rowptr[Mt];
         std::vector<int> st, ssrc;
         for (int64_t i = 0; i < Mt; i++) {
             if (ns[i] > 1) {
@@ -372,19 +451,35 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
             CK(upload(mem, &pl.d_self_tgt, st));
             CK(upload(mem, &pl.d_self_src, ssrc));
         }
-        CK(upload(mem, &pl.d_rowptr, rowptr));
         size_t freeb = 0, totb = 0;
         CK(cudaMemGetInfo(&freeb, &totb));
-        size_t need = (size_t)pl.n_slots * (sizeof(int) + sizeof(double) + pl.NW * sizeof(T));
+        size_t need = fac ? (size_t)nall * (sizeof(int) + sizeof(double) + sizeof(TabPair<T>)) +
+                                (size_t)(P.W - 1) * M * 36 * sizeof(T)
+                          : (size_t)nall * (sizeof(int) + sizeof(double) + pl.NW * sizeof(T));
         if (need + (size_t)(1ull << 30) > freeb) {
-            err = "local weights need " + std::to_string(need >> 20) + " MiB of device memory";
+            err = "local part needs " + std::to_string(need >> 20) + " MiB of device memory";
             return WFP_ENOMEM;
         }
-        CK(mem.alloc(&pl.d_col, pl.n_slots));
-        CK(d_r.alloc(pl.n_slots));
-        CK(cudaMemset(d_r.p, 0, std::max<size_t>(pl.n_slots, 1) * sizeof(double)));
+        Tmp<int64_t> d_rpall;
+        Tmp<int> d_colall;
+        int64_t* rp = nullptr;
+        int* colp = nullptr;
+        if (fac) {
+            CK(upload_tmp(d_rpall, rowptr));
+            CK(d_colall.alloc(nall));
+            rp = d_rpall.p;
+            colp = d_colall.p;
+        } else {
+            CK(upload(mem, &pl.d_rowptr, rowptr));
+            CK(mem.alloc(&pl.d_col, nall));
+            rp = pl.d_rowptr;
+            colp = pl.d_col;
+            pl.n_slots = nall;
+        }
+        CK(d_r.alloc(nall));
+        CK(cudaMemset(d_r.p, 0, std::max<size_t>(nall, 1) * sizeof(double)));
         k_nbr<<<nblk(Mt, 128), 128>>>(1, Mt, (const double2*)d_t.p, (const double2*)d_s.p, d_cs.p, nc, cs, P.delta,
-                                      rc, nullptr, nullptr, nullptr, pl.d_rowptr, pl.d_col, d_r.p);
+                                      rc, nullptr, nullptr, nullptr, rp, colp, d_r.p);
         CK(cudaGetLastError());
         // ---- local weights (Sec. 6)
         const int ng = 20;
@@ -399,16 +494,14 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(upload_tmp(d_gw, gw));
         CK(upload_tmp(d_wl, wl));
         CK(upload_tmp(d_bls, bls));
-        T* eta = nullptr;
-        CK(mem.alloc(&eta, (size_t)pl.n_slots * pl.NW));
-        pl.d_eta = eta;
         const double* Cls = pl.opts.local_interp == WFP_INTERP_LAGRANGE ? nullptr : d_bls.p;
         // Chebyshev table of the weights on the delay intervals k >= 1: direct weights at the nodes
         // (device), coefficients (host); pairs then evaluate the table instead of the quadrature
         Tmp<double> d_tab;
+        std::vector<double> tab;
         if (P.W >= 2) {
             const int N = kEtaChebDeg + 1, nn = (P.W - 1) * N;
-            std::vector<double> rn(nn), vals((size_t)nn * P.nmax), tab;
+            std::vector<double> rn(nn), vals((size_t)nn * P.nmax);
             for (int k = 1; k < P.W; k++)
                 for (int j = 0; j < N; j++) {
                     const double v = 0.5 * (std::cos(kPi * (j + 0.5) / N) + 1.0) * std::sqrt(P.dt);
@@ -424,8 +517,60 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
             eta_table_coefficients(P.W, P.nmax, vals, tab);
             CK(upload_tmp(d_tab, tab));
         }
+        Tmp<double> d_nr;  // factored form: distances of the near pairs
+        const double* rslot = d_r.p;
+        if (fac) {
+            // split every row: r >= dt -> table pairs (factored weights), r < dt -> near pairs
+            Tmp<int> d_nt, d_nn;
+            CK(d_nt.alloc(Mt));
+            CK(d_nn.alloc(Mt));
+            k_split<T><<<nblk(Mt, 128), 128>>>(0, Mt, rp, colp, d_r.p, P.dt, P.W, d_nt.p, d_nn.p, nullptr, nullptr,
+                                               nullptr, nullptr, nullptr);
+            CK(cudaGetLastError());
+            std::vector<int> nt(Mt), nnr(Mt);
+            CK(cudaMemcpy(nt.data(), d_nt.p, Mt * sizeof(int), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(nnr.data(), d_nn.p, Mt * sizeof(int), cudaMemcpyDeviceToHost));
+            std::vector<int64_t> trow(Mt + 1, 0), nrow(Mt + 1, 0);
+            for (int64_t i = 0; i < Mt; i++) {
+                trow[i + 1] = trow[i] + nt[i];
+                nrow[i + 1] = nrow[i] + nnr[i];
+            }
+            pl.n_tab = trow[Mt];
+            pl.n_near = nrow[Mt];
+            pl.n_slots = pl.n_near;
+            CK(upload(mem, &pl.d_trow, trow));
+            CK(upload(mem, &pl.d_rowptr, nrow));
+            TabPair<T>* tp = nullptr;
+            CK(mem.alloc(&tp, (size_t)pl.n_tab));
+            pl.d_tpair = tp;
+            CK(mem.alloc(&pl.d_col, (size_t)pl.n_near));
+            CK(d_nr.alloc(pl.n_near));
+            k_split<T><<<nblk(Mt, 128), 128>>>(1, Mt, rp, colp, d_r.p, P.dt, P.W, nullptr, nullptr, pl.d_trow,
+                                               pl.d_rowptr, tp, pl.d_col, d_nr.p);
+            CK(cudaGetLastError());
+            rslot = d_nr.p;
+            // series coefficients by window position, cut after NC terms
+            pl.NC = factored_nc_supported(choose_nc(tab, P.W, P.nmax, sizeof(T) == 8), sizeof(T) == 8);
+            // (FP32 blocks lane-interleaved by coefficient residue, see k_local_cheb4)
+            std::vector<T> ctab((size_t)(P.W - 1) * 32 * pl.NC, (T)0);
+            const int N = kEtaChebDeg + 1;
+            for (int kk = 0; kk < P.W - 1; kk++)
+                for (int l = 0; l < P.nmax; l++)
+                    for (int c = 0; c < std::min(pl.NC, N); c++)
+                        ctab[((size_t)kk * 32 + (32 - P.nmax + l)) * pl.NC + (sizeof(T) == 8 ? c : cheb4_position(c))] =
+                            (T)tab[((size_t)kk * P.nmax + l) * N + c];
+            T* dct = nullptr;
+            CK(upload(mem, &dct, ctab));
+            pl.d_ctab = dct;
+            T* dy = nullptr;
+            CK(mem.alloc(&dy, (size_t)(P.W - 1) * M * pl.NC));
+            pl.d_ycoef = dy;
+        }
+        T* eta = nullptr;
+        CK(mem.alloc(&eta, (size_t)pl.n_slots * pl.NW));
+        pl.d_eta = eta;
         if (pl.n_slots > 0) {
-            k_eta<T><<<nblk(pl.n_slots, 128), 128>>>(pl.n_slots, d_r.p, P.dt, P.W, P.p, P.nmax, pl.NW, pl.d_phicoef,
+            k_eta<T><<<nblk(pl.n_slots, 128), 128>>>(pl.n_slots, rslot, P.dt, P.W, P.p, P.nmax, pl.NW, pl.d_phicoef,
                                                      d_gx.p, d_gw.p, ng, d_wl.p, Cls, d_tab.p, eta);
             CK(cudaGetLastError());
         }
@@ -855,13 +1000,14 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(cudaStreamSynchronize(cudaStreamPerThread));
     }
 
-    // ---- local-part autotuner: all variants give the same bits; keep the fastest
-    if (pl.NW == 32 && Mt > 0) {
-        const int ov = pl.opts.local_variant;
-        if (ov < 0 || ov > kLocalVariants) {
-            err = "local_variant must be 0 (auto) or 1.." + std::to_string(kLocalVariants);
-            return WFP_EINVAL;
-        }
+    // ---- local-part autotuner (stored form): all variants give the same bits; keep the fastest
+    const int ov = pl.opts.local_variant;
+    if (ov < 0 || ov > kLocalVariants) {
+        err = "local_variant must be 0 (auto) or 1.." + std::to_string(kLocalVariants);
+        return WFP_EINVAL;
+    }
+    if (pl.local_factored) pl.local_variant = 0;
+    if (pl.NW == 32 && Mt > 0 && !pl.local_factored) {
         if (ov > 0) {
             pl.local_variant = ov;
         } else {

@@ -62,6 +62,16 @@ struct Plan {
     int64_t* d_rowptr = nullptr;
     int* d_col = nullptr;
     void* d_eta = nullptr;       // NW = 32: row position 32 - nmax + l holds eta_l (aligned with d_siglin)
+    // factored form (WFP_LOCAL_FACTORED): pairs with r >= dt as {source | (k - 1) << 26, x} with x the
+    // Chebyshev variable of their delay interval k; the pairs with r < dt keep d_rowptr / d_col /
+    // d_eta above (rows not padded)
+    bool local_factored = false;
+    int NC = 0;                  // Chebyshev coefficients kept per interval (multiple of 4)
+    int64_t n_tab = 0, n_near = 0;
+    int64_t* d_trow = nullptr;   // [Mt + 1] table-pair rows
+    void* d_tpair = nullptr;     // [n_tab] TabPair<T>
+    void* d_ctab = nullptr;      // [W - 1][32][NC] series coefficients by window position, reduced precision
+    void* d_ycoef = nullptr;     // [W - 1][M][NC] per step: windows contracted with d_ctab
 
     // sigma storage
     void* d_sigwin = nullptr;    // [M][NW] window of the last NW levels (slot = level & (NW-1)), reduced precision
@@ -196,7 +206,8 @@ wfp_status plan_step_device(Plan& pl, double* u_dev, std::string& err);
 void local_bulk_setup();  // raises the dynamic shared-memory limit of the staged local kernels
 constexpr int kLocalVariants = 5;  // 1 = warp-vector loads, 2..5 = bulk-staged configurations
 void local_launch(const Plan& pl, int variant, cudaStream_t st);
-void local_run(const Plan& pl, cudaStream_t st);  // the plan's local-part kernel
+void local_run(const Plan& pl, cudaStream_t st);  // the plan's local-part kernel(s)
+int factored_nc_supported(int nc, bool fp64);      // coefficient count the factored kernels use for nc
 // one spreading launch with the given tiling (plan-time autotuner and step loop)
 void spread_launch(const Plan& pl, int ts, int ch, int lag, int n_tiles, const int* txy, const int* tptr,
                    const int* tsrc, void* sp, cudaStream_t st);  // input already in d_sig_in

@@ -124,8 +124,8 @@ bool estimate_bytes(const Request& r, const wfp_opts& o, int64_t bytes[2], std::
         next[j] = head[(size_t)iy * nc + ix];
         head[(size_t)iy * nc + ix] = (int)j;
     }
-    int64_t pairs = 0;
-    const double d2max = (P.delta / sc) * (P.delta / sc);
+    int64_t pairs = 0, near = 0;
+    const double d2max = (P.delta / sc) * (P.delta / sc), d2near = (P.dt / sc) * (P.dt / sc);
     for (int64_t i = 0; i < r.Mt; i++) {
         double x = r.tgt[2 * i], y = r.tgt[2 * i + 1];
         int ix, iy;
@@ -136,6 +136,7 @@ bool estimate_bytes(const Request& r, const wfp_opts& o, int64_t bytes[2], std::
                     double dx = x - r.src[2 * (size_t)j], dy = y - r.src[2 * (size_t)j + 1];
                     double d2 = dx * dx + dy * dy;
                     if (d2 > 0 && d2 < d2max) pairs++;
+                    if (d2 > 0 && d2 < d2near) near++;
                 }
     }
     const double s = (P.precision == WFP_FP64) ? 8.0 : 4.0, c = 2 * s;
@@ -149,11 +150,17 @@ bool estimate_bytes(const Request& r, const wfp_opts& o, int64_t bytes[2], std::
         for (int64_t q = 0; q <= a && a * a + q * q <= R * R; q++)
             if (!seen[(size_t)(a * a + q * q)]) seen[(size_t)(a * a + q * q)] = 1, n_kappa += 1;
     const int NW = P.nmax <= 32 ? 32 : 64;
+    P.M = r.M;
+    const bool fac = local_form_of(P, o) == WFP_LOCAL_FACTORED;
     const double nf = P.nf, nh2 = P.nf / 2 + 1, nc1 = P.Nh + 1, nb = P.nb;
     for (int store = 0; store < 2; store++) {
     const bool rec = P.lag_active && !store;
     double b = (double)(r.par.size() + std::max<size_t>(1, r.out_steps.size()) * r.Mt) * 8.0;  // request buffers
-    b += pairs * (NW * s + 4) + (r.Mt + 1) * 8.0;                                     // local part
+    if (fac)  // factored form: pair records, near rows, per-step contraction (at most 36 coefficients)
+        b += (pairs - near) * (2 * s) + near * (NW * s + 4) + 2 * (r.Mt + 1) * 8.0 +
+             (P.W - 1) * (double)r.M * 36 * s + (P.W - 1) * 32 * 36 * s;
+    else
+        b += pairs * (NW * s + 4) + (r.Mt + 1) * 8.0;                                  // local part
     const bool keep = store && P.lag_active;  // the S history is stored only while the lag is in use
     b += modes * (8 + 4 + 32 + (keep ? P.L + P.W : P.W) * c + (rec ? P.W * c : 0));   // modes, state, S
     b += n_kappa * (4 * P.W * s + 24);                                                  // taps per |k|

@@ -17,6 +17,7 @@ WFP_OK, WFP_EINVAL, WFP_ENOMEM, WFP_ECUDA, WFP_ESTATE, WFP_ETIMEOUT, WFP_EUNSUPP
 FP64, MIXED = 0, 1
 LAG_AUTO, LAG_RECOMPUTE, LAG_STORE = 0, 1, 2
 INTERP_HYBRID, INTERP_LAGRANGE = 0, 1
+LOCAL_AUTO, LOCAL_STORED, LOCAL_FACTORED = 0, 1, 2
 
 _c_i64 = ctypes.c_int64
 _c_dbl = ctypes.c_double
@@ -29,7 +30,7 @@ class wfp_opts(ctypes.Structure):
                 ("soe_nodes", ctypes.c_int), ("exclude_self", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("use_graph", ctypes.c_int), ("lag_mode", ctypes.c_int), ("spread_tile", ctypes.c_int),
                 ("spread_chunk", ctypes.c_int), ("local_variant", ctypes.c_int), ("local_interp", ctypes.c_int),
-                ("delta", _c_dbl)]
+                ("delta", _c_dbl), ("local_form", ctypes.c_int)]
 
 
 class wfp_info(ctypes.Structure):
@@ -43,7 +44,8 @@ class wfp_info(ctypes.Structure):
                 ("upsampfac", _c_dbl), ("n_pairs", _c_i64), ("n_self", _c_i64), ("lag_active", ctypes.c_int),
                 ("far_active", ctypes.c_int), ("precision", ctypes.c_int), ("device_bytes", _c_i64),
                 ("lag_store", ctypes.c_int), ("s_levels", _c_i64), ("spread_tile", ctypes.c_int),
-                ("spread_chunk", ctypes.c_int), ("local_variant", ctypes.c_int)]
+                ("spread_chunk", ctypes.c_int), ("local_variant", ctypes.c_int), ("local_form", ctypes.c_int),
+                ("local_nc", ctypes.c_int), ("n_near_pairs", _c_i64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

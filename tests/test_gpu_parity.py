@@ -89,8 +89,47 @@ def test_mixed_precision_small():
     # FP32 spreading / FFT / taps / weights, FP64 state and accumulation (wfp_opts.precision = MIXED)
     wl = inputs.small(150, 3.0, 250, seed=1)
     got, info, _ = run_plan(wl, precision=1)
+    assert info["local_form"] == 2 and 12 <= info["local_nc"] <= 36
     steps = [60, 130, 200, 250]
     ref = oracle_at(wl, None, steps)
     e = rel_errors(got[np.array(steps) - 1], ref)
     print("\nmixed rel L2:", np.array2string(e, precision=2))
     assert e.max() <= 1e-5
+
+
+def test_factored_local_part_fp64_equals_stored_rows():
+    # the factored local part (each interval's weight series contracted with the source windows
+    # first, then summed against T_c(x_ij) per pair) regroups the same table weights as the stored
+    # rows: in FP64 with every coefficient kept, the two agree to rounding.  Targets: on the
+    # sources (rows with near pairs, r < dt) and off the curve (rows without)
+    from paper_2604_07170_gb300 import wfp
+    wl = inputs.small(200, 4.0, 120, seed=2, curve=True)
+    rng = np.random.default_rng(7)
+    tgt = np.vstack([wl.src_xy[::3], rng.uniform(0.0, 4.0, (40, 2))])
+    a, ia, ca = run_plan(wl, tgt_xy=tgt, local_form=wfp.LOCAL_STORED)
+    b, ib, cb = run_plan(wl, tgt_xy=tgt, local_form=wfp.LOCAL_FACTORED)
+    assert ia["local_form"] == 1 and ib["local_form"] == 2 and ib["local_nc"] == 36
+    assert 0 < ib["n_near_pairs"] < ib["n_pairs"] == ia["n_pairs"]
+    ul_a, ul_b = ca["last"][0], cb["last"][0]
+    d_loc = np.linalg.norm(ul_b - ul_a) / np.linalg.norm(ul_a)
+    d_all = np.linalg.norm(b - a) / np.linalg.norm(a)
+    print(f"\nfactored vs stored FP64: local {d_loc:.2e}, field {d_all:.2e}")
+    assert d_loc <= 1e-13 and d_all <= 1e-13
+
+
+def test_factored_local_part_mixed_against_oracle():
+    # the mixed path's factored local part (series cut where its tail drops below FP32 rounding,
+    # FP32 contraction and recurrences, compensated sums) against the oracle and beside the stored
+    # FP32 rows: same error level
+    from paper_2604_07170_gb300 import wfp
+    wl = inputs.small(300, 4.0, 220, seed=3, curve=True)
+    steps = [60, 120, 180, 220]
+    ref = oracle_at(wl, None, steps)
+    e = {}
+    for form in (wfp.LOCAL_STORED, wfp.LOCAL_FACTORED):
+        got, info, _ = run_plan(wl, precision=1, local_form=form)
+        assert info["local_form"] == form
+        e[form] = rel_errors(got[np.array(steps) - 1], ref)
+    print("\nmixed stored / factored rel L2:", np.array2string(e[1], precision=2), np.array2string(e[2], precision=2))
+    assert e[2].max() <= max(2 * e[1].max(), 1e-6)
+    assert e[2].max() <= 1e-5

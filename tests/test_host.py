@@ -43,6 +43,10 @@ def test_invalid_arguments_are_rejected_on_the_host():
         assert ei.value.code == wfp.WFP_EINVAL
     with pytest.raises(wfp.WFPError):
         wfp.select_params(10.0, 0.1, 100, K0, 1e-6, precision=7)
+    for lf in (-1, 3):
+        with pytest.raises(wfp.WFPError) as ei:
+            wfp.select_params(10.0, 0.1, 100, K0, 1e-6, local_form=lf)
+        assert ei.value.code == wfp.WFP_EINVAL
 
 
 def test_parameters_reproduce_the_papers_printed_example():
