@@ -117,13 +117,10 @@ WFP_HD inline double cheb_phi(const double* coef, double x) {
 
 // Form of the local weights a plan uses (wfp_opts.local_form): WFP_LOCAL_STORED or
 // WFP_LOCAL_FACTORED, or -1 when the factored form is asked for but cannot serve the plan.  The
-// factored form needs a 32-level window (nmax <= 32), at least one table interval (W >= 2) and
-// source indices below 2^26 (packed with the interval index into one word per pair), and
-// (W - 1) M 32-coefficient blocks of 16-byte vectors indexable in 32 bits.
-constexpr int kFactoredMaxSources = 1 << 26;
+// factored form needs a 32-level window (nmax <= 32), at least one table interval (W >= 2), and
+// (W - 1) M coefficient blocks indexable in 32 bits (with room for 16-byte vector indices).
 inline int local_form_of(const Params& P, const wfp_opts& o) {
-    const bool fits = P.nmax <= 32 && P.W >= 2 && P.M < kFactoredMaxSources &&
-                      (double)(P.W - 1) * (double)P.M * 8.0 < 4294967296.0;
+    const bool fits = P.nmax <= 32 && P.W >= 2 && (double)(P.W - 1) * (double)P.M * 8.0 < 4294967296.0;
     if (o.local_form == WFP_LOCAL_FACTORED) return fits ? WFP_LOCAL_FACTORED : -1;
     if (o.local_form == WFP_LOCAL_STORED) return WFP_LOCAL_STORED;
     return (fits && P.precision == WFP_MIXED) ? WFP_LOCAL_FACTORED : WFP_LOCAL_STORED;

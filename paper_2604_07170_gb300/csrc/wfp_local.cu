@@ -91,14 +91,14 @@ static void factored_nc(const Plan& pl, cudaStream_t st) {
         k_ycoef<T, NC><<<dim3(nblk_u(pl.M, 128), (unsigned)nk), 128, 0, st>>>(pl.M, (const T*)pl.d_siglin,
                                                                             (const T*)pl.d_ctab, (T*)pl.d_ycoef);
         k_local_cheb<T, NC><<<nblk_u(pl.Mt * 32, 256), 256, 0, st>>>(
-            pl.Mt, pl.M, pl.d_trow, (const TabPair<T>*)pl.d_tpair, (const T*)pl.d_ycoef, pl.d_rowptr, pl.d_col,
+            pl.Mt, pl.d_trow, (const TabPair<T>*)pl.d_tpair, (const T*)pl.d_ycoef, pl.d_rowptr, pl.d_col,
             (const T*)pl.d_eta, (const T*)pl.d_siglin, pl.d_uloc);
     } else {
         constexpr int KC = 64 / NC;  // intervals per block of k_ycoef4
         k_ycoef4<NC><<<dim3(nblk_u(pl.M, 32), (unsigned)((nk + KC - 1) / KC)), 128, 0, st>>>(
             pl.M, nk, (const float*)pl.d_siglin, (const float*)pl.d_ctab, (float*)pl.d_ycoef);
-        k_local_cheb4<NC><<<nblk_u(pl.Mt * 32, 256), 256, 0, st>>>(
-            pl.Mt, pl.M, pl.d_trow, (const TabPair<float>*)pl.d_tpair, (const float*)pl.d_ycoef, pl.d_rowptr,
+        k_local_cheb2<NC><<<nblk_u(pl.Mt * 32, 256), 256, 0, st>>>(
+            pl.Mt, pl.d_trow, (const TabPair<float>*)pl.d_tpair, (const float*)pl.d_ycoef, pl.d_rowptr,
             pl.d_col, (const float*)pl.d_eta, (const float*)pl.d_siglin, pl.d_uloc);
     }
 }

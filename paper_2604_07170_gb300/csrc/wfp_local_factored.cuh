@@ -11,28 +11,27 @@
 
 namespace wfp {
 
-// One pair of the factored local part: source index j and delay-interval index k - 1 packed as
-// j | (k - 1) << 26, and the interval's Chebyshev variable x = 2 sqrt(((k+1) dt - r) / dt) - 1.
+// One pair of the factored local part: the index (k - 1) M + j of its source's coefficient block
+// for delay interval k, and the interval's Chebyshev variable x = 2 sqrt(((k+1) dt - r) / dt) - 1.
 template <typename T>
 struct TabPair;
 template <>
 struct __align__(8) TabPair<float> {
-    unsigned ck;
+    unsigned blk;
     float x;
 };
 template <>
 struct __align__(16) TabPair<double> {
-    unsigned ck, pad;
+    unsigned blk, pad;
     double x;
 };
-constexpr unsigned kTabPairSrcMask = (1u << 26) - 1;
 
 // ------------------------------------------------------------------ factored local part
 // On a delay interval [k dt, (k+1) dt], k >= 1, each weight is a Chebyshev series in the interval's
 // variable x(r): eta_l(r) = sum_c C[k][l][c] T_c(x(r)).  Summing over the levels first,
 //   sum_l eta_l(r_ij) sigma_j,l = sum_c T_c(x_ij) y[k][j][c],   y[k][j][c] = sum_l C[k][l][c] sigma_j,l,
 // so one contraction per source and interval per step (k_ycoef) replaces a weight row per pair, and
-// a pair needs only (j, k, x): 8 bytes instead of 32 weights.  y is small (sources x intervals x NC)
+// a pair needs only its block index and x: 8 bytes instead of 32 weights.  y is small (sources x intervals x NC)
 // and gathered from L2 by the pairs.
 
 template <typename T>
@@ -118,11 +117,10 @@ __device__ __forceinline__ TabPair<double> load_pair(const TabPair<double>* p) {
 }
 
 template <typename T, int NC>
-__device__ __forceinline__ T tab_pair_value(const TabPair<T>& e, int64_t M, const T* __restrict__ y) {
+__device__ __forceinline__ T tab_pair_value(const TabPair<T>& e, const T* __restrict__ y) {
     using V = typename Vec16<T>::type;
     constexpr int EV = 16 / (int)sizeof(T);
-    const int64_t j = (int64_t)(e.ck & kTabPairSrcMask), kk = (int64_t)(e.ck >> 26);
-    const V* yb = (const V*)(y + (kk * M + j) * NC);
+    const V* yb = (const V*)(y + (int64_t)e.blk * NC);
     T yy[NC];
 #pragma unroll
     for (int v = 0; v < NC / EV; v++) unpack16<T>(__ldg(yb + v), yy + v * EV);
@@ -133,7 +131,7 @@ __device__ __forceinline__ T tab_pair_value(const TabPair<T>& e, int64_t M, cons
 // table pairs 32 apart), then its near pairs (r < dt, stored 32-level rows against the source's
 // window), one lane each.
 template <typename T, int NC>
-__global__ void __launch_bounds__(256) k_local_cheb(int64_t Mt, int64_t M, const int64_t* __restrict__ trow,
+__global__ void __launch_bounds__(256) k_local_cheb(int64_t Mt, const int64_t* __restrict__ trow,
                                                     const TabPair<T>* __restrict__ tp, const T* __restrict__ y,
                                                     const int64_t* __restrict__ nrow, const int* __restrict__ ncol,
                                                     const T* __restrict__ neta, const T* __restrict__ siglin,
@@ -143,22 +141,10 @@ __global__ void __launch_bounds__(256) k_local_cheb(int64_t Mt, int64_t M, const
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= Mt) return;
-    float sm = 0.f, cm = 0.f;  // FP32: compensated sum
-    double d = 0.0;            // FP64
+    static_assert(sizeof(T) == 8, "the FP32 form is k_local_cheb2");
+    double d = 0.0;
     const int64_t p1 = trow[row + 1];
-    int64_t p = trow[row] + lane;
-    if constexpr (sizeof(T) == 4) {
-        for (; p + 32 < p1; p += 64) {
-            const TabPair<T> e0 = load_pair(tp + p), e1 = load_pair(tp + p + 32);
-            const float v0 = tab_pair_value<T, NC>(e0, M, y);
-            const float v1 = tab_pair_value<T, NC>(e1, M, y);
-            kahan_add(sm, cm, v0);
-            kahan_add(sm, cm, v1);
-        }
-        if (p < p1) kahan_add(sm, cm, tab_pair_value<T, NC>(load_pair(tp + p), M, y));
-    } else {
-        for (; p < p1; p += 32) d += tab_pair_value<T, NC>(load_pair(tp + p), M, y);
-    }
+    for (int64_t p = trow[row] + lane; p < p1; p += 32) d += tab_pair_value<T, NC>(load_pair(tp + p), y);
     for (int64_t q = nrow[row] + lane; q < nrow[row + 1]; q += 32) {
         const V* E = (const V*)(neta + q * 32);
         const V* X = (const V*)(siglin + (int64_t)ncol[q] * 32);
@@ -174,89 +160,90 @@ __global__ void __launch_bounds__(256) k_local_cheb(int64_t Mt, int64_t M, const
                 a1 = fma(e[u + 1], x[u + 1], a1);
             }
         }
-        if constexpr (sizeof(T) == 4)
-            kahan_add(sm, cm, a0 + a1);
-        else
-            d += a0 + a1;
+        d += a0 + a1;
     }
-    double tot = (sizeof(T) == 4) ? (double)sm - (double)cm : d;
-    tot = warp_sum(tot);
+    const double tot = warp_sum(d);
     if (lane == 0) uloc[row] = tot;
 }
 
 
-// FP32 form.  A pair's y block (NC = 16 or 32 floats, 64 or 128 contiguous bytes) is read by four
-// lanes, 16 bytes each per load, so one warp load gathers eight whole blocks (eight L1 wavefronts)
-// instead of 32 scattered 16-byte pieces.  The block is stored lane-interleaved by coefficient
-// residue: position 16 v + 4 q + e holds c = q + 4 (4 v + e), so lane q holds T_q, T_{q+4}, ... and
-// runs the stride-4 recurrence T_{c+4} = 2 T_4 T_c - T_{c-4} (with T_{q-4} = T_{4-q}).
-template <int NV>
-__device__ __forceinline__ float cheb_quarter(float x, const float* yy, int q) {
+// FP32 form.  A pair's y block (NC = 16 or 32 floats, 64 or 128 contiguous bytes) is read by two
+// lanes with 32-byte loads, so a warp load gathers sixteen whole 64-byte blocks (sixteen L1
+// wavefronts for sixteen pairs).  The block is stored lane-interleaved by coefficient parity:
+// position 16 v + 8 q + e holds c = q + 2 (8 v + e), so lane q holds T_q, T_{q+2}, ... and runs the
+// stride-2 recurrence T_{c+2} = 2 T_2 T_c - T_{c-2} (with T_{q-2} = T_{2-q}).
+__device__ __forceinline__ void ldg_v8(const float* p, float* o) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]), "=f"(o[7])
+        : "l"(p));
+}
+
+template <int NH>
+__device__ __forceinline__ float cheb_half(float x, const float* yy, int q) {
     const float x2 = x + x;
-    const float t2 = fmaf(x2, x, -1.f), t3 = fmaf(x2, t2, -x), t4 = fmaf(x2, t3, -t2);
-    float a = q == 0 ? 1.f : (q == 1 ? x : (q == 2 ? t2 : t3));  // T_q
-    float b = q == 0 ? t4 : (q == 1 ? t3 : (q == 2 ? t2 : x));   // T_{q-4} = T_{4-q}
-    const float w4 = t4 + t4;
+    const float t2 = fmaf(x2, x, -1.f);
+    float a = q ? x : 1.f;   // T_q
+    float b = q ? x : t2;    // T_{q-2} = T_{2-q}
+    const float w2 = t2 + t2;
     float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-    for (int m = 0; m < 4 * NV; m++) {
+    for (int m = 0; m < NH; m++) {
         if (m & 1)
             s1 = fmaf(a, yy[m], s1);
         else
             s0 = fmaf(a, yy[m], s0);
-        const float n = fmaf(w4, a, -b);
+        const float n = fmaf(w2, a, -b);
         b = a;
         a = n;
     }
     return s0 + s1;
 }
 
-// One warp per target row; lanes (g, q) = (lane / 4, lane % 4) take the row's table pairs 8 apart,
-// four per lane in flight (their records, then their blocks, loaded before any is used; the four
-// values are added, then compensated into the lane's FP32 sum).  Near pairs (r < dt): eight lanes
-// per stored row, one 16-byte vector each.  The 32 lanes' sums are added in FP64 at the end.  Block
-// indices are 32-bit (the plan keeps (W - 1) M NC / 4 below 2^32).
+// One warp per target row; lanes (g, q) = (lane / 2, lane % 2) take the row's table pairs 16 apart,
+// four per lane per round: the round's blocks are gathered while the next round's records load,
+// and the four values are added, then compensated into the lane's FP32 sum.  Near pairs (r < dt): eight lanes
+// per stored row, one 16-byte vector each.  The 32 lanes' sums are added in FP64 at the end.
 template <int NC>
-__global__ void __launch_bounds__(256) k_local_cheb4(int64_t Mt, int64_t M, const int64_t* __restrict__ trow,
+__global__ void __launch_bounds__(256) k_local_cheb2(int64_t Mt, const int64_t* __restrict__ trow,
                                                      const TabPair<float>* __restrict__ tp, const float* __restrict__ y,
                                                      const int64_t* __restrict__ nrow, const int* __restrict__ ncol,
                                                      const float* __restrict__ neta, const float* __restrict__ siglin,
                                                      double* __restrict__ uloc) {
     static_assert(NC == 16 || NC == 32, "blocks of 16 or 32 coefficients");
-    constexpr int NV = NC / 16;  // 16-byte loads per lane per pair
+    constexpr int NL = NC / 16;  // 32-byte loads per lane per pair
     constexpr int U = 4;
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= Mt) return;
-    const int q = lane & 3, g = lane >> 2;
-    const uint32_t Mu = (uint32_t)M;
+    const int q = lane & 1, g = lane >> 1;
     float sm = 0.f, cm = 0.f;
-    const float4* Y = (const float4*)y;
     const int64_t p1 = trow[row + 1];
+    // software pipeline: the records of the next U pairs are loaded while this group's blocks are
+    // gathered and summed; past the row's end a record reads as block 0 with its value masked
+    const TabPair<float> none{0u, 0.f};
     int64_t p = trow[row] + g;
-    for (; p + 8 * (U - 1) < p1; p += 8 * U) {
-        TabPair<float> e[U];
-        float yy[U][4 * NV];
+    TabPair<float> en[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) e[u] = load_pair(tp + p + 8 * u);
+    for (int u = 0; u < U; u++) en[u] = (p + 16 * u < p1) ? load_pair(tp + p + 16 * u) : none;
+    for (; p < p1; p += 16 * U) {
+        TabPair<float> e[U];
+        float yy[U][NC / 2];
 #pragma unroll
         for (int u = 0; u < U; u++) {
-            const uint32_t blk = (e[u].ck >> 26) * Mu + (e[u].ck & kTabPairSrcMask);
+            e[u] = en[u];
 #pragma unroll
-            for (int v = 0; v < NV; v++) unpack16<float>(__ldg(Y + (blk * (4 * NV) + 4 * v + q)), yy[u] + 4 * v);
+            for (int v = 0; v < NL; v++) ldg_v8(y + (size_t)e[u].blk * NC + 16 * v + 8 * q, yy[u] + 8 * v);
         }
+        const int64_t pn = p + 16 * U;
+#pragma unroll
+        for (int u = 0; u < U; u++) en[u] = (pn + 16 * u < p1) ? load_pair(tp + pn + 16 * u) : none;
         float acc = 0.f;
 #pragma unroll
-        for (int u = 0; u < U; u++) acc += cheb_quarter<NV>(e[u].x, yy[u], q);
+        for (int u = 0; u < U; u++) {
+            const float v = cheb_half<NC / 2>(e[u].x, yy[u], q);
+            if (p + 16 * u < p1) acc += v;
+        }
         kahan_add(sm, cm, acc);
-    }
-    for (; p < p1; p += 8) {
-        const TabPair<float> e = load_pair(tp + p);
-        const uint32_t blk = (e.ck >> 26) * Mu + (e.ck & kTabPairSrcMask);
-        float yy[4 * NV];
-#pragma unroll
-        for (int v = 0; v < NV; v++) unpack16<float>(__ldg(Y + (blk * (4 * NV) + 4 * v + q)), yy + 4 * v);
-        kahan_add(sm, cm, cheb_quarter<NV>(e.x, yy, q));
     }
     const int c8 = lane & 7, g8 = lane >> 3;
     const float4* E = (const float4*)neta;
@@ -322,11 +309,11 @@ __global__ void __launch_bounds__(128) k_ycoef4(int64_t M, int nk, const float* 
     }
 }
 
-// position of coefficient c in an FP32 block of NC (16 or 32): the inverse of c = q + 4 (4 v + e)
-// at position 16 v + 4 q + e
-__host__ __device__ inline int cheb4_position(int c) {
-    const int q = c & 3, m = c >> 2;
-    return 16 * (m >> 2) + 4 * q + (m & 3);
+// position of coefficient c in an FP32 block of NC (16 or 32): the inverse of c = q + 2 (8 v + e)
+// at position 16 v + 8 q + e
+__host__ __device__ inline int cheb2_position(int c) {
+    const int q = c & 1, m = c >> 1;
+    return 16 * (m >> 3) + 8 * q + (m & 7);
 }
 
 }  // namespace wfp

@@ -153,11 +153,12 @@ void build_eta_table(double dt, int W, int p, int nmax, const double* phicoef, c
 }
 
 // Factored form: split the pairs of each target row by delay interval -- r >= dt to the table
-// pairs (interval k = floor(r / dt) and its Chebyshev variable, exactly as eta_from_table forms
-// them), r < dt to the near pairs that keep stored weight rows; row order is kept.  Pass 0 counts,
+// pairs (the block (k - 1) M + j of interval k = floor(r / dt) and its Chebyshev variable, exactly
+// as eta_from_table forms them), r < dt to the near pairs that keep stored weight rows; row order
+// is kept.  Pass 0 counts,
 // pass 1 writes.
 template <typename T>
-__global__ void k_split(int pass, int64_t Mt, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+__global__ void k_split(int pass, int64_t Mt, int64_t M, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
                         const double* __restrict__ rr, double dt, int W, int* __restrict__ ntab,
                         int* __restrict__ nnear, const int64_t* __restrict__ trow, const int64_t* __restrict__ nrow,
                         TabPair<T>* __restrict__ tp, int* __restrict__ ncol, double* __restrict__ nr) {
@@ -174,7 +175,7 @@ __global__ void k_split(int pass, int64_t Mt, const int64_t* __restrict__ rowptr
                 k = k < 1 ? 1 : (k > W - 1 ? W - 1 : k);
                 const double v = sqrt(fmax(0.0, (k + 1) * dt - r));
                 TabPair<T> e;
-                e.ck = (unsigned)col[s] | ((unsigned)(k - 1) << 26);
+                e.blk = (unsigned)((int64_t)(k - 1) * M + col[s]);
                 if constexpr (sizeof(T) == 8) e.pad = 0u;
                 e.x = (T)(2.0 * v / sqrt(dt) - 1.0);
                 tp[a + ca] = e;
@@ -403,7 +404,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
     // ---- neighbour search (Sec. 6: N_delta = {j : 0 < r_ij < delta})
     const int form = local_form_of(P, pl.opts);
     if (form < 0) {
-        err = "local_form WFP_LOCAL_FACTORED needs nmax <= 32, W >= 2 and fewer than 2^26 sources";
+        err = "local_form WFP_LOCAL_FACTORED needs nmax <= 32, W >= 2 and 8 (W - 1) M < 2^32";
         return WFP_EUNSUPPORTED;
     }
     pl.local_factored = form == WFP_LOCAL_FACTORED;
@@ -524,7 +525,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
             Tmp<int> d_nt, d_nn;
             CK(d_nt.alloc(Mt));
             CK(d_nn.alloc(Mt));
-            k_split<T><<<nblk(Mt, 128), 128>>>(0, Mt, rp, colp, d_r.p, P.dt, P.W, d_nt.p, d_nn.p, nullptr, nullptr,
+            k_split<T><<<nblk(Mt, 128), 128>>>(0, Mt, M, rp, colp, d_r.p, P.dt, P.W, d_nt.p, d_nn.p, nullptr, nullptr,
                                                nullptr, nullptr, nullptr);
             CK(cudaGetLastError());
             std::vector<int> nt(Mt), nnr(Mt);
@@ -545,19 +546,19 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
             pl.d_tpair = tp;
             CK(mem.alloc(&pl.d_col, (size_t)pl.n_near));
             CK(d_nr.alloc(pl.n_near));
-            k_split<T><<<nblk(Mt, 128), 128>>>(1, Mt, rp, colp, d_r.p, P.dt, P.W, nullptr, nullptr, pl.d_trow,
+            k_split<T><<<nblk(Mt, 128), 128>>>(1, Mt, M, rp, colp, d_r.p, P.dt, P.W, nullptr, nullptr, pl.d_trow,
                                                pl.d_rowptr, tp, pl.d_col, d_nr.p);
             CK(cudaGetLastError());
             rslot = d_nr.p;
             // series coefficients by window position, cut after NC terms
             pl.NC = factored_nc_supported(choose_nc(tab, P.W, P.nmax, sizeof(T) == 8), sizeof(T) == 8);
-            // (FP32 blocks lane-interleaved by coefficient residue, see k_local_cheb4)
+            // (FP32 blocks lane-interleaved by coefficient parity, see k_local_cheb2)
             std::vector<T> ctab((size_t)(P.W - 1) * 32 * pl.NC, (T)0);
             const int N = kEtaChebDeg + 1;
             for (int kk = 0; kk < P.W - 1; kk++)
                 for (int l = 0; l < P.nmax; l++)
                     for (int c = 0; c < std::min(pl.NC, N); c++)
-                        ctab[((size_t)kk * 32 + (32 - P.nmax + l)) * pl.NC + (sizeof(T) == 8 ? c : cheb4_position(c))] =
+                        ctab[((size_t)kk * 32 + (32 - P.nmax + l)) * pl.NC + (sizeof(T) == 8 ? c : cheb2_position(c))] =
                             (T)tab[((size_t)kk * P.nmax + l) * N + c];
             T* dct = nullptr;
             CK(upload(mem, &dct, ctab));
