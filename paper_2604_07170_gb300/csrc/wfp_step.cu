@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(256) k_modes(
         }
         hxd = hx, hyd = hy, gxd = gx, gyd = gy;
     } else {
-        static_assert(sizeof(T) == 8, "the FP32 mode update is k_modes_pair");
+        static_assert(sizeof(T) == 8, "the FP32 mode update is k_modes_one");
     }
     double c = rot[3 * kid], sk = rot[3 * kid + 1], ks = rot[3 * kid + 2];
     double2 a = alpha[m], ad = alphad[m];
@@ -339,147 +339,144 @@ __global__ void __launch_bounds__(256) k_modes(
     }
 }
 
-// Mixed-path mode update: two threads per mode.  Thread r = 0 forms h, r = 1 forms g (Eq. hggrid)
-// from its half of the taps (hi/lo pairs, one float4 per level) with error-free products summed in
-// double-float, so that the FIR adding a level and the one removing it L steps later round alike
-// and nothing persists in alpha.  The newest current and lagged levels come from registers.
-// Thread 0 advances alpha with h and writes the type-2 coefficient, thread 1 advances alpha-dot
-// with g (Eq. alphakEvolution, FP64).
+// Mixed-path mode update, one thread per mode.  Both FIRs of Eq. hggrid -- h with the taps {p, pA},
+// g with {q, qA}, hi/lo pairs -- are formed from one set of ring loads with error-free products
+// summed in double-float, so that the FIR adding a level and the one removing it L steps later
+// round alike and nothing persists in alpha.  The newest current and lagged levels come from
+// registers; a level's taps for both FIRs are one 32-byte load.  Then alpha and alpha-dot advance
+// (Eq. alphakEvolution, FP64) and the type-2 coefficient is written.  (Two threads per mode, one
+// per FIR, gave the same bits with every ring value loaded twice: 6% slower at 10^4 points and 33%
+// at 10^6.)
+__device__ __forceinline__ void ldg_v8f(const float* p, float4& a, float4& b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
 template <bool COMPACT>
-__global__ void __launch_bounds__(256) k_modes_pair(
+__global__ void __launch_bounds__(256) k_modes_one(
     const int64_t* __restrict__ d_step, int64_t n_modes, int W, int L, int Nh, int nf, const int2* __restrict__ mode_n,
     const int* __restrict__ mode_k, const float* __restrict__ facf, float coef2, const float2* __restrict__ tc_cur,
     const float2* __restrict__ tc_lag, float2* __restrict__ ring, float2* __restrict__ ring_lag, int R_cur, int R_lag,
     int lag_off, int write_lag, const float* __restrict__ taps, const double* __restrict__ rot,
     double2* __restrict__ alpha, double2* __restrict__ alphad, float2* __restrict__ td, int64_t near_sq,
     const double2* __restrict__ aF, int64_t n_far_now) {
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t m = tid >> 1;
-    const int r = (int)(tid & 1);
-    const bool valid = m < n_modes;
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_modes) return;
     const int64_t n = *d_step + 1;
     const bool lag = (n - L >= 1);
-    int2 nn = make_int2(0, 0);
-    int kid = 0;
-    int64_t gi = 0;
-    float f = 0.f;
-    float2 s_cur = make_float2(0.f, 0.f), s_lag = make_float2(0.f, 0.f);
     const int slot = (int)(n % R_cur);
     const int slot_lag = (int)((((n - L + lag_off) % R_lag) + R_lag) % R_lag);  // level n - L
-    if (valid) {
-        nn = mode_n[m];
-        kid = mode_k[m];
-        const int row = nn.x < 0 ? nn.x + nf : nn.x;
-        gi = (int64_t)row * (Nh + 1) + nn.y;
-        f = facf[nn.x < 0 ? -nn.x : nn.x] * facf[nn.y];  // deconvolution, FP32 like the transform
+    const int2 nn = mode_n[m];
+    const int kid = mode_k[m];
+    const int row = nn.x < 0 ? nn.x + nf : nn.x;
+    const int64_t gi = (int64_t)row * (Nh + 1) + nn.y;
+    const float f = facf[nn.x < 0 ? -nn.x : nn.x] * facf[nn.y];  // deconvolution, FP32 like the transform
+    float2 s_cur, s_lag = make_float2(0.f, 0.f);
+    {
         const float2 t = tc_cur[gi];
         s_cur.x = t.x * f;
         s_cur.y = -t.y * f;
-        if (r == 0) ring[(int64_t)slot * n_modes + m] = s_cur;
-        if (lag) {
-            if (write_lag) {  // lagged NUFFT result: level n - L
-                const float2 u = tc_lag[gi];
-                s_lag.x = u.x * f;
-                s_lag.y = -u.y * f;
-                if (r == 1) ring_lag[(int64_t)slot_lag * n_modes + m] = s_lag;
-            } else {
-                s_lag = ring_lag[(int64_t)slot_lag * n_modes + m];
-            }
+    }
+    ring[(int64_t)slot * n_modes + m] = s_cur;
+    if (lag) {
+        if (write_lag) {  // lagged NUFFT result: level n - L
+            const float2 u = tc_lag[gi];
+            s_lag.x = u.x * f;
+            s_lag.y = -u.y * f;
+            ring_lag[(int64_t)slot_lag * n_modes + m] = s_lag;
+        } else {
+            s_lag = ring_lag[(int64_t)slot_lag * n_modes + m];
         }
     }
-    // near history truncated at |k| <= K (Eq. uhtraptrunc): modes beyond carry only S
-    const bool near = valid && (int64_t)nn.x * nn.x + (int64_t)nn.y * nn.y <= near_sq;
-    float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f;
-    if (near) {
-        // this thread's FIR taps per level: {tap, tapA} hi and lo (float4), or {tap hi, tap lo}
-        // (float2) when the plan's lag never activates
-        const float4* tp4 = (const float4*)(taps + (int64_t)kid * 8 * W) + r;
-        const float2* tp2 = (const float2*)(taps + (int64_t)kid * 4 * W) + r;
-        constexpr int U = 4;  // levels whose loads are in flight together
-        int sl = slot, sll = slot_lag;
-        for (int j0 = 0; j0 < W; j0 += U) {
-            float2 a[U], b[U];
-            float4 t4[U];
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                const int j = j0 + u;
-                if (j < W) {
-                    if constexpr (COMPACT) {
-                        const float2 t2 = tp2[2 * j];
-                        t4[u] = make_float4(t2.x, 0.f, t2.y, 0.f);
-                    } else {
-                        t4[u] = tp4[2 * j];
-                    }
-                    if (j == 0) {
-                        a[u] = s_cur;
-                        b[u] = s_lag;
-                    } else {
-                        const int s1 = sl - u < 0 ? sl - u + R_cur : sl - u;
-                        a[u] = ring[(int64_t)s1 * n_modes + m];
-                        if (!COMPACT && lag) {
-                            const int s2 = sll - u < 0 ? sll - u + R_lag : sll - u;
-                            b[u] = ring_lag[(int64_t)s2 * n_modes + m];
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                if (j0 + u < W) {
-                    df_acc(xh, xl, t4[u].x, t4[u].z, a[u].x);
-                    df_acc(yh, yl, t4[u].x, t4[u].z, a[u].y);
-                    if (!COMPACT && lag) {
-                        df_acc(xh, xl, -t4[u].y, -t4[u].w, b[u].x);
-                        df_acc(yh, yl, -t4[u].y, -t4[u].w, b[u].y);
-                    }
-                }
-            }
-            sl = sl - U < 0 ? sl - U + R_cur : sl - U;
-            sll = sll - U < 0 ? sll - U + R_lag : sll - U;
-        }
-    }
-    const double vx = (double)xh + (double)xl, vy = (double)yh + (double)yl;  // h (r = 0) or g (r = 1)
-    if (!valid) return;
-    const float cf = coef2 * f;  // type-2 coefficient in the grid precision
-    if (!near) {  // only the far coefficient alpha_F, if any
-        if (r == 0) {
-            const double2 af = (m < n_far_now) ? aF[m] : make_double2(0.0, 0.0);
-            float2 o;
-            o.x = (float)af.x * cf;
-            o.y = -(float)af.y * cf;
-            td[gi] = o;
-            if (nn.y == 0 && nn.x > 0) {
-                o.y = (float)af.y * cf;
-                td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
-            }
+    const float cf = coef2 * f;
+    if ((int64_t)nn.x * nn.x + (int64_t)nn.y * nn.y > near_sq) {  // only the far coefficient, if any
+        const double2 af = (m < n_far_now) ? aF[m] : make_double2(0.0, 0.0);
+        float2 o;
+        o.x = (float)af.x * cf;
+        o.y = -(float)af.y * cf;
+        td[gi] = o;
+        if (nn.y == 0 && nn.x > 0) {
+            o.y = (float)af.y * cf;
+            td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
         }
         return;
     }
+    // h: (hxh, hxl, hyh, hyl); g: (gxh, gxl, gyh, gyl)
+    float hxh = 0.f, hxl = 0.f, hyh = 0.f, hyl = 0.f, gxh = 0.f, gxl = 0.f, gyh = 0.f, gyl = 0.f;
+    const float* tk = taps + (int64_t)kid * (COMPACT ? 4 : 8) * W;
+    constexpr int U = 2;  // levels whose loads are in flight together
+    int sl = slot, sll = slot_lag;
+    for (int j0 = 0; j0 < W; j0 += U) {
+        float2 a[U], b[U];
+        float4 th[U], tg[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int j = j0 + u;
+            if (j < W) {
+                if constexpr (COMPACT) {
+                    const float4 t = *(const float4*)(tk + 4 * j);  // {p hi, p lo, q hi, q lo}
+                    th[u] = make_float4(t.x, 0.f, t.y, 0.f);
+                    tg[u] = make_float4(t.z, 0.f, t.w, 0.f);
+                } else {
+                    ldg_v8f(tk + 8 * j, th[u], tg[u]);
+                }
+                if (j == 0) {
+                    a[u] = s_cur;
+                    b[u] = s_lag;
+                } else {
+                    const int s1 = sl - u < 0 ? sl - u + R_cur : sl - u;
+                    a[u] = ring[(int64_t)s1 * n_modes + m];
+                    if (!COMPACT && lag) {
+                        const int s2 = sll - u < 0 ? sll - u + R_lag : sll - u;
+                        b[u] = ring_lag[(int64_t)s2 * n_modes + m];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (j0 + u < W) {
+                df_acc(hxh, hxl, th[u].x, th[u].z, a[u].x);
+                df_acc(hyh, hyl, th[u].x, th[u].z, a[u].y);
+                if (!COMPACT && lag) {
+                    df_acc(hxh, hxl, -th[u].y, -th[u].w, b[u].x);
+                    df_acc(hyh, hyl, -th[u].y, -th[u].w, b[u].y);
+                }
+                df_acc(gxh, gxl, tg[u].x, tg[u].z, a[u].x);
+                df_acc(gyh, gyl, tg[u].x, tg[u].z, a[u].y);
+                if (!COMPACT && lag) {
+                    df_acc(gxh, gxl, -tg[u].y, -tg[u].w, b[u].x);
+                    df_acc(gyh, gyl, -tg[u].y, -tg[u].w, b[u].y);
+                }
+            }
+        }
+        sl = sl - U < 0 ? sl - U + R_cur : sl - U;
+        sll = sll - U < 0 ? sll - U + R_lag : sll - U;
+    }
+    const double hx = (double)hxh + (double)hxl, hy = (double)hyh + (double)hyl;
+    const double gx = (double)gxh + (double)gxl, gy = (double)gyh + (double)gyl;
     const double c = rot[3 * kid], sk = rot[3 * kid + 1], ks = rot[3 * kid + 2];
     const double2 a = alpha[m], ad = alphad[m];
-    if (r == 0) {  // alpha(t + dt) = cos(k dt) alpha + sin(k dt)/k alphadot + h
-        double2 an;
-        an.x = fma(c, a.x, fma(sk, ad.x, vx));
-        an.y = fma(c, a.y, fma(sk, ad.y, vy));
-        alpha[m] = an;
-        if (m < n_far_now) {  // near plus far history
-            const double2 af = aF[m];
-            an.x += af.x;
-            an.y += af.y;
-        }
-        float2 o;
-        o.x = (float)an.x * cf;
-        o.y = -(float)an.y * cf;
-        td[gi] = o;
-        if (nn.y == 0 && nn.x > 0) {
-            o.y = (float)an.y * cf;
-            td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
-        }
-    } else {  // alphadot(t + dt) = -k sin(k dt) alpha + cos(k dt) alphadot + g
-        double2 adn;
-        adn.x = fma(-ks, a.x, fma(c, ad.x, vx));
-        adn.y = fma(-ks, a.y, fma(c, ad.y, vy));
-        alphad[m] = adn;
+    double2 an, adn;
+    an.x = fma(c, a.x, fma(sk, ad.x, hx));
+    an.y = fma(c, a.y, fma(sk, ad.y, hy));
+    adn.x = fma(-ks, a.x, fma(c, ad.x, gx));
+    adn.y = fma(-ks, a.y, fma(c, ad.y, gy));
+    alpha[m] = an;
+    alphad[m] = adn;
+    if (m < n_far_now) {  // near plus far history
+        const double2 af = aF[m];
+        an.x += af.x;
+        an.y += af.y;
+    }
+    float2 o;
+    o.x = (float)an.x * cf;
+    o.y = -(float)an.y * cf;
+    td[gi] = o;
+    if (nn.y == 0 && nn.x > 0) {
+        o.y = (float)an.y * cf;
+        td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
     }
 }
 
@@ -798,8 +795,8 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err, cudaEvent_
             pl.lag_off, pl.lag_store ? 0 : 1, (const T*)pl.d_taps, pl.d_rot, pl.d_alpha, pl.d_alphad, (C*)pl.d_td,
             near_sq, pl.d_aF, n_far_now);
     } else {
-        auto kern = pl.compact_taps ? k_modes_pair<true> : k_modes_pair<false>;
-        kern<<<nblk(2 * pl.n_modes, 256), 256, 0, st>>>(
+        auto kern = pl.compact_taps ? k_modes_one<true> : k_modes_one<false>;
+        kern<<<nblk(pl.n_modes, 256), 256, 0, st>>>(
             pl.d_step, pl.n_modes, P.W, P.L, P.Nh, P.nf, pl.d_mode_n, pl.d_mode_k, pl.d_facf, (float)coef2,
             (const float2*)pl.d_tc_cur, (const float2*)pl.d_tc_lag, (float2*)pl.d_ring, (float2*)pl.d_ring_lag,
             pl.R_cur, pl.R_lag, pl.lag_off, pl.lag_store ? 0 : 1, (const float*)pl.d_taps, pl.d_rot, pl.d_alpha,
