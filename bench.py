@@ -527,8 +527,8 @@ def main():
                                f"{wl.meta['box']:g}x{wl.meta['box']:g}-wavelength box, dt={wl.dt}, N_t={wl.n_steps}, "
                                f"tol={wl.tol:g}, {args.precision}",
                    "timed_steps": [r["n_last"] - K + 1, r["n_last"]],
-                   "l2": "inputs larger than L2 (local weights %.2f GB per step)" % (
-                       info["n_pairs"] * 32 * (8 if fp64 else 4) / 1e9),
+                   "l2": "inputs larger than L2 (%.2f GB of algorithmic bytes per step across the parts)" % (
+                       sum(v["bytes"] for v in part_model(info, wl.M, wl.M, fp64).values()) / 1e9),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "W": info["W"], "p": info["p"], "L": info["L"], "N_modes_half": info["n_modes"],
                    "nf": info["nf"], "n_pairs": info["n_pairs"], "n_lambda": info["n_lambda"],
