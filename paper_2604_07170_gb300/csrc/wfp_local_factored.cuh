@@ -30,9 +30,10 @@ struct __align__(16) TabPair<double> {
 // On a delay interval [k dt, (k+1) dt], k >= 1, each weight is a Chebyshev series in the interval's
 // variable x(r): eta_l(r) = sum_c C[k][l][c] T_c(x(r)).  Summing over the levels first,
 //   sum_l eta_l(r_ij) sigma_j,l = sum_c T_c(x_ij) y[k][j][c],   y[k][j][c] = sum_l C[k][l][c] sigma_j,l,
-// so one contraction per source and interval per step (k_ycoef) replaces a weight row per pair, and
-// a pair needs only its block index and x: 8 bytes instead of 32 weights.  y is small (sources x intervals x NC)
-// and gathered from L2 by the pairs.
+// so one contraction per source and interval per step (k_ycoef4; k_ycoef in FP64) replaces a weight
+// row per pair, and a pair needs only its block index and x: 8 bytes instead of 32 weights.  y holds
+// sources x intervals x NC values; the pairs of neighbouring targets gather the same blocks, mostly
+// from L2.
 
 template <typename T>
 __device__ __forceinline__ void unpack16(const typename Vec16<T>::type& q, T* out);
@@ -50,7 +51,8 @@ __device__ __forceinline__ void unpack16<double>(const double2& q, double* out) 
 }
 
 // y[kk][j][c] = sum_i ctab[kk][i][c] siglin[j][i] (window position i = 32 - nmax + l holds level l;
-// the coefficients of the unused positions are zero).  Thread = source, blockIdx.y = interval; the
+// the coefficients of the unused positions are zero).  The FP64 form (all 33 coefficients, used to
+// check the factoring against the stored rows): thread = source, blockIdx.y = interval; the
 // interval's coefficients are staged in shared memory and read as warp-uniform broadcasts.
 template <typename T, int NC>
 __global__ void __launch_bounds__(128) k_ycoef(int64_t M, const T* __restrict__ siglin, const T* __restrict__ ctab,
