@@ -379,16 +379,19 @@ def parts_roofline(per: dict, fp64: bool) -> dict:
 
 
 def source_hash(kernel: str = "local") -> str:
-    """Hash of the sources a kernel is built from (its counters go stale when they change)."""
+    """Hash of the code a kernel is built from, comments and blank lines left out (its counters go
+    stale when the code changes)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2604_07170_gb300", "csrc")
     files = {"local": ("wfp_local_kernels.cuh", "wfp_ptx.h", "wfp_dev.h"),
              "local_factored": ("wfp_local_factored.cuh", "wfp_local_kernels.cuh", "wfp_dev.h")}.get(
         kernel, ("wfp_step.cu", "wfp_dev.h"))
     for fn in files:
-        with open(os.path.join(d, fn), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(d, fn)) as f:
+            code = re.sub(r"//[^\n]*", "", f.read())
+        h.update("\n".join(ln.strip() for ln in code.splitlines() if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 
