@@ -33,6 +33,20 @@ wfp_status wfp_debug_eta(double r, double dt, int W, int p, double eps, double b
 wfp_status wfp_debug_eta_table(double r, double dt, int W, int p, double eps, double band_limit, int ng, double* eta);
 
 /*
+ * The per-interval Chebyshev table behind wfp_debug_eta_table and the coefficient count the factored
+ * local part keeps (wfp_opts.local_form): coefficients of the weights on the delay intervals
+ * k = 1..W-1, tab[((k - 1) nmax + l) 33 + c] for the series sum_c tab[..][c] T_c(x) in
+ * x = 2 sqrt(((k+1) dt - r) / dt) - 1 (nmax = W + 1 + p/2).  *nc = the coefficients kept by a plan
+ * of the given precision (WFP_MIXED: the first multiple of 4, at least 16 and at most 32, whose
+ * dropped tail is within 2^-25 of the interval's weight scale; WFP_FP64: all, reported as 36 with
+ * zero padding); *tail = the largest dropped tail over intervals and levels relative to the
+ * interval's weight scale max_l sum_c |tab|.  tab may be NULL; else (W - 1) * nmax * 33 doubles.
+ * Arguments otherwise as wfp_debug_eta; host only.
+ */
+wfp_status wfp_debug_factored_table(double dt, int W, int p, double eps, double band_limit, int ng, int precision,
+                                    int* nc, double* tail, double* tab);
+
+/*
  * Near-history FIR taps at wavenumber magnitude kappa (Lemma 4.2, Eq. hggrid), dt folded in:
  * taps[0..W) = p_m, [W..2W) = q_m, [2W..3W) = pA_m, [3W..4W) = qA_m; lagshift = A+ - delta.
  * rot = {cos(kappa dt), sin(kappa dt)/kappa, kappa sin(kappa dt)}.  taps: 4W doubles, rot: 3.

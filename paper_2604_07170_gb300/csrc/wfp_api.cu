@@ -426,6 +426,28 @@ wfp_status wfp_debug_eta_table(double r, double dt, int W, int p, double eps, do
     return WFP_OK;
 }
 
+wfp_status wfp_debug_factored_table(double dt, int W, int p, double eps, double band_limit, int ng, int precision,
+                                    int* nc, double* tail, double* tab_out) {
+    if (!nc || !tail || W < 2 || W > 59 || p < 2 || p > kMaxP || (p & 1) || ng < 2 || ng > 64 ||
+        (precision != WFP_FP64 && precision != WFP_MIXED))
+        return fail(WFP_EINVAL, "bad argument");
+    int nmax = W + 1 + p / 2;
+    if (nmax > kMaxLevels) return fail(WFP_EINVAL, "W + 1 + p/2 too large");
+    std::vector<double> phic, gx(ng), gw(ng), wl(p);
+    build_phi_table(std::log(1.0 / eps), phic);
+    gauss_legendre(ng, gx.data(), gw.data());
+    lagrange_ref_weights(p, wl.data());
+    std::vector<double> cls, tab;
+    double Omega = std::max(band_limit, 1e-3 / dt);
+    if (band_limit >= 0) build_ls_cheb(nmax, dt, Omega, kLsIntervals * dt, cls);
+    build_eta_table(dt, W, p, nmax, phic.data(), gx.data(), gw.data(), ng, wl.data(),
+                    band_limit >= 0 ? cls.data() : nullptr, tab);
+    *nc = factored_nc_supported(factored_nc_choice(tab, W, nmax, precision == WFP_FP64), precision == WFP_FP64);
+    *tail = factored_tail(tab, W, nmax, std::min(*nc, kEtaChebDeg + 1));
+    if (tab_out) std::copy(tab.begin(), tab.end(), tab_out);
+    return WFP_OK;
+}
+
 wfp_status wfp_debug_taps(double kappa, double dt, int W, double eps, double lagshift, double* taps, double* rot) {
     if (!taps || !rot || W < 2 || W > 59) return fail(WFP_EINVAL, "bad argument");
     double b = std::log(1.0 / eps), delta = W * dt;

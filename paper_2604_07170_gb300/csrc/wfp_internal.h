@@ -73,6 +73,10 @@ void build_ls_cheb(int nmax, double dt, double Omega, double span, std::vector<d
 void build_eta_table(double dt, int W, int p, int nmax, const double* phicoef, const double* gx, const double* gw,
                      int ng, const double* wl, const double* Cls, std::vector<double>& tab);
 void build_ls_cheb_into(int nmax, double dt, double Omega, double span, double* C);  // no heap use
+// coefficients the factored local part keeps from that table, and the relative tail it drops (see
+// wfp_debug_factored_table)
+int factored_nc_choice(const std::vector<double>& tab, int W, int nmax, bool fp64);
+double factored_tail(const std::vector<double>& tab, int W, int nmax, int nc);
 // W, p, nmax and eps of the local part from dt, K0 (band limit) and tol (no heap use)
 wfp_status local_params(double dt, double K0, double tol, const wfp_opts& o, double* eps, int* W, int* p, int* nmax,
                         const char** why);

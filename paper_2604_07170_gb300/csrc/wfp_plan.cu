@@ -195,31 +195,35 @@ __global__ void k_split(int pass, int64_t Mt, int64_t M, const int64_t* __restri
     }
 }
 
-// Coefficients to keep per interval in the factored form: the smallest multiple of 4 whose dropped
-// tail, sum_{c >= NC} |C[k][l][c]|, is at most 2^-25 of the interval's weight scale
-// max_l sum_c |C[k][l][c]| for every level and interval (reduced precision); every coefficient in
-// FP64.
-static int choose_nc(const std::vector<double>& tab, int W, int nmax, bool fp64) {
+// Largest dropped tail sum_{c >= nc} |C[k][l][c]| of the factored form's per-interval series, over
+// intervals and levels, relative to the interval's weight scale max_l sum_c |C[k][l][c]|.
+double factored_tail(const std::vector<double>& tab, int W, int nmax, int nc) {
     const int N = kEtaChebDeg + 1;
+    double w = 0.0;
+    for (int kk = 0; kk < W - 1; kk++) {
+        double scale = 0.0;
+        for (int l = 0; l < nmax; l++) {
+            double a = 0.0;
+            for (int c = 0; c < N; c++) a += std::fabs(tab[((size_t)kk * nmax + l) * N + c]);
+            scale = std::max(scale, a);
+        }
+        for (int l = 0; l < nmax; l++) {
+            double t = 0.0;
+            for (int c = nc; c < N; c++) t += std::fabs(tab[((size_t)kk * nmax + l) * N + c]);
+            if (scale > 0.0) w = std::max(w, t / scale);
+        }
+    }
+    return w;
+}
+
+// Coefficients to keep per interval in the factored form: the smallest multiple of 4 whose dropped
+// tail is at most 2^-25 of the interval's weight scale (reduced precision; 36 if even 32 are not
+// enough); every coefficient (36, zero-padded) in FP64.
+int factored_nc_choice(const std::vector<double>& tab, int W, int nmax, bool fp64) {
     if (fp64 || tab.empty()) return 36;
     const double thr = std::ldexp(1.0, -25);
-    for (int nc = 8; nc <= 32; nc += 4) {
-        bool ok = true;
-        for (int kk = 0; kk < W - 1 && ok; kk++) {
-            double scale = 0.0;
-            for (int l = 0; l < nmax; l++) {
-                double a = 0.0;
-                for (int c = 0; c < N; c++) a += std::fabs(tab[((size_t)kk * nmax + l) * N + c]);
-                scale = std::max(scale, a);
-            }
-            for (int l = 0; l < nmax && ok; l++) {
-                double tail = 0.0;
-                for (int c = nc; c < N; c++) tail += std::fabs(tab[((size_t)kk * nmax + l) * N + c]);
-                ok = tail <= thr * scale;
-            }
-        }
-        if (ok) return nc;
-    }
+    for (int c = 8; c <= 32; c += 4)
+        if (factored_tail(tab, W, nmax, c) <= thr) return c;
     return 36;
 }
 
@@ -551,7 +555,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
             CK(cudaGetLastError());
             rslot = d_nr.p;
             // series coefficients by window position, cut after NC terms
-            pl.NC = factored_nc_supported(choose_nc(tab, P.W, P.nmax, sizeof(T) == 8), sizeof(T) == 8);
+            pl.NC = factored_nc_supported(factored_nc_choice(tab, P.W, P.nmax, sizeof(T) == 8), sizeof(T) == 8);
             // (FP32 blocks lane-interleaved by coefficient parity, see k_local_cheb2)
             std::vector<T> ctab((size_t)(P.W - 1) * 32 * pl.NC, (T)0);
             const int N = kEtaChebDeg + 1;

@@ -54,7 +54,7 @@ class wfp_info(ctypes.Structure):
 _lib = None
 
 # every symbol declared in include/wfp.h and include/wfp_debug.h
-EXPORTS = ["wfp_debug_eta_table", "wfp_opts_default", "wfp_plan_create", "wfp_step", "wfp_destroy", "wfp_plan_get_info",
+EXPORTS = ["wfp_debug_eta_table", "wfp_debug_factored_table", "wfp_opts_default", "wfp_plan_create", "wfp_step", "wfp_destroy", "wfp_plan_get_info",
            "wfp_step_components", "wfp_select_params", "wfp_status_string", "wfp_last_error",
            "wfp_profile", "wfp_profile_read", "wfp_local_noalloc", "wfp_debug_eta", "wfp_debug_taps", "wfp_debug_phi",
            "wfp_debug_soe", "wfp_debug_hankel", "wfp_debug_bounded_wait", "wfp_checkpoint_size",
@@ -109,6 +109,9 @@ def lib():
     L.wfp_debug_eta.argtypes = [_c_dbl, _c_dbl, ctypes.c_int, ctypes.c_int, _c_dbl, _c_dbl, ctypes.c_int, _pd]
     L.wfp_debug_eta_table.argtypes = [_c_dbl, _c_dbl, ctypes.c_int, ctypes.c_int, _c_dbl, _c_dbl, ctypes.c_int, _pd]
     L.wfp_debug_eta_table.restype = ctypes.c_int
+    L.wfp_debug_factored_table.argtypes = [_c_dbl, ctypes.c_int, ctypes.c_int, _c_dbl, _c_dbl, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int), _pd, _pd]
+    L.wfp_debug_factored_table.restype = ctypes.c_int
     L.wfp_debug_taps.argtypes = [_c_dbl, _c_dbl, ctypes.c_int, _c_dbl, _c_dbl, _pd, _pd]
     L.wfp_debug_phi.argtypes = [_c_dbl, _c_dbl, _c_dbl, _pd, _pd, _pd]
     L.wfp_debug_soe.argtypes = [_c_dbl, ctypes.c_int, ctypes.c_int, _pd, _pd]
@@ -336,6 +339,18 @@ class Server:
 
 
 # ------------------------------------------------------------------ host-only diagnostics
+def debug_factored_table(dt, W, p=20, eps=1e-8, band_limit=0.0, ng=20, precision=MIXED):
+    """(coefficients kept, largest dropped relative tail, table [W-1][nmax][33]) of the factored local
+    part's per-interval Chebyshev series."""
+    nmax = W + 1 + p // 2
+    tab = np.zeros((W - 1, nmax, 33))
+    nc = ctypes.c_int(0)
+    tail = np.zeros(1)
+    _check(lib().wfp_debug_factored_table(dt, W, p, eps, band_limit, ng, precision, ctypes.byref(nc), _dptr(tail),
+                                          _dptr(tab)), "wfp_debug_factored_table")
+    return nc.value, float(tail[0]), tab
+
+
 def debug_eta(r, dt, W, p=20, eps=1e-8, band_limit=0.0, ng=20) -> np.ndarray:
     out = np.zeros(W + 1 + p // 2)
     _check(lib().wfp_debug_eta(r, dt, W, p, eps, band_limit, ng, _dptr(out)), "wfp_debug_eta")

@@ -254,3 +254,32 @@ def test_local_weight_table_matches_the_quadrature():
             b = wfp.debug_eta_table(r, dt, W, p, eps, K0)
             worst = max(worst, float(np.max(np.abs(a - b))))
         assert worst <= 1e-13, (dt, W, worst)
+
+
+def test_factored_local_series_cut_against_the_quadrature():
+    # the factored local part (mixed path) keeps the first NC Chebyshev coefficients of each delay
+    # interval's weight series; the dropped tail must bound the error against the direct quadrature
+    # of the weights, and the regrouping sum_l eta_l sigma_l = sum_c T_c(x) (sum_l C_lc sigma_l) must
+    # hold for the library's own table
+    from numpy.polynomial import chebyshev as C
+    dt, W, p, eps = 0.1, 23, 16, 1e-9
+    K0 = 2 * np.pi + np.sqrt(2 * np.log(1 / eps))
+    nc, tail, tab = wfp.debug_factored_table(dt, W, p, eps, K0, 20, precision=wfp.MIXED)
+    assert nc == 16 and 0 < tail <= 2.0 ** -25
+    nc64, tail64, _ = wfp.debug_factored_table(dt, W, p, eps, K0, 20, precision=wfp.FP64)
+    assert nc64 == 36 and tail64 == 0.0
+    rng = np.random.default_rng(5)
+    sig = rng.standard_normal(tab.shape[1])
+    # the table's own accuracy is ~1e-15 of the largest weights (intervals far out carry tiny ones)
+    floor = 1e-13 * np.abs(tab).sum(axis=2).max()
+    for k in range(1, W):
+        scale = np.abs(tab[k - 1]).sum(axis=1).max()
+        for r in rng.uniform(k * dt, (k + 1) * dt, 3):
+            x = 2 * np.sqrt(((k + 1) * dt - r) / dt) - 1
+            quad = wfp.debug_eta(r, dt, W, p, eps, K0)
+            full = np.array([C.chebval(x, tab[k - 1, l]) for l in range(tab.shape[1])])
+            cut = np.array([C.chebval(x, tab[k - 1, l, :nc]) for l in range(tab.shape[1])])
+            assert np.abs(full - quad).max() <= floor
+            assert np.abs(cut - quad).max() <= tail * scale + floor
+            y = tab[k - 1, :, :nc].T @ sig  # per-coefficient contraction of the window
+            assert abs(C.chebval(x, y) - cut @ sig) <= 1e-14 * scale * np.abs(sig).sum()
