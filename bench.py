@@ -189,7 +189,7 @@ def part_model(info: dict, M: int, Mt: int, fp64: bool) -> dict:
     m["interp"] = (nb * nb * s + Mt * (2 * w * s + 4 + 8), 2 * Mt * w * w)
     # two-stage pruned FFTs: R2C over the nb band rows, C2C over the N_h + 1 kept columns (and back)
     nh2, nc1, lg = nfg // 2 + 1, info["Nh"] + 1, math.log2(nfg)
-    fft_b = nb * nfg * s + nb * nh2 * c + 2 * nfg * nc1 * c
+    fft_b = nb * nfg * s + nb * nh2 * c + 2 * nb * nc1 * c + 2 * nfg * nc1 * c  # rows, band transpose, columns
     fft_f = nb * 2.5 * nfg * lg + nc1 * 5 * nfg * lg
     m["fft_type1"] = (spreads * fft_b, spreads * fft_f)
     m["fft_type2"] = (fft_b, fft_f)

@@ -867,6 +867,8 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(mem.alloc(&tb, (size_t)nf * nh2));
         pl.d_tb_cur = tb;
         CK(mem.alloc(&tc, (size_t)nf * nc1));
+        pl.d_tcol_cur = tc;
+        CK(mem.alloc(&tc, (size_t)nf * nc1));
         pl.d_tc_cur = tc;
         if (P.lag_active && !pl.lag_store) {
             CK(mem.alloc(&sp, (size_t)P.nb * nf));
@@ -874,12 +876,16 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
             CK(mem.alloc(&tb, (size_t)nf * nh2));
             pl.d_tb_lag = tb;
             CK(mem.alloc(&tc, (size_t)nf * nc1));
+            pl.d_tcol_lag = tc;
+            CK(mem.alloc(&tc, (size_t)nf * nc1));
             pl.d_tc_lag = tc;
         } else {
             pl.d_tc_lag = pl.d_tc_cur;  // never read while the lag is inactive
         }
         CK(mem.alloc(&td, (size_t)nf * nc1));
         pl.d_td = td;
+        CK(mem.alloc(&td, (size_t)nf * nc1));
+        pl.d_te2 = td;
         CK(mem.alloc(&te, (size_t)nf * nh2));
         pl.d_te = te;
         CK(mem.alloc(&tf, (size_t)P.nb * nf));
@@ -889,11 +895,10 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         int emb_r[1] = {(int)nf}, emb_c[1] = {(int)nh2};
         CKF(cufftPlanMany(&pl.fftA, 1, n, emb_r, 1, (int)nf, emb_c, 1, (int)nh2, dbl ? CUFFT_D2Z : CUFFT_R2C, P.nb));
         pl.fft_made[0] = true;
-        CKF(cufftPlanMany(&pl.fftB, 1, n, emb_r, (int)nh2, 1, emb_r, (int)nc1, 1, dbl ? CUFFT_Z2Z : CUFFT_C2C,
-                          (int)nc1));
+        // column transforms over the column-major [Nh+1][nf] layout: contiguous vectors
+        CKF(cufftPlanMany(&pl.fftB, 1, n, emb_r, 1, (int)nf, emb_r, 1, (int)nf, dbl ? CUFFT_Z2Z : CUFFT_C2C, (int)nc1));
         pl.fft_made[1] = true;
-        CKF(cufftPlanMany(&pl.fftBi, 1, n, emb_r, (int)nc1, 1, emb_r, (int)nh2, 1, dbl ? CUFFT_Z2Z : CUFFT_C2C,
-                          (int)nc1));
+        CKF(cufftPlanMany(&pl.fftBi, 1, n, emb_r, 1, (int)nf, emb_r, 1, (int)nf, dbl ? CUFFT_Z2Z : CUFFT_C2C, (int)nc1));
         pl.fft_made[2] = true;
         CKF(cufftPlanMany(&pl.fftAi, 1, n, emb_c, 1, (int)nh2, emb_r, 1, (int)nf, dbl ? CUFFT_Z2D : CUFFT_C2R, P.nb));
         pl.fft_made[3] = true;

@@ -94,12 +94,15 @@ struct Plan {
     int* d_tile_src = nullptr;   // sources per tile (internal index), fixed order
     void* d_sp_cur = nullptr;    // [nb][nf] real spread grid (current)
     void* d_sp_lag = nullptr;    // [nb][nf] real spread grid (lagged)
-    void* d_tb_cur = nullptr;    // [nf][nf/2+1] complex (rows outside the band stay zero)
+    void* d_tb_cur = nullptr;    // [nf][nf/2+1] complex: row transforms of the band (band rows only)
     void* d_tb_lag = nullptr;
-    void* d_tc_cur = nullptr;    // [nf][Nh+1] complex: type-1 result before deconvolution
+    void* d_tcol_cur = nullptr;  // [Nh+1][nf] complex: their kept columns, column-major (rows outside the band stay zero)
+    void* d_tcol_lag = nullptr;
+    void* d_tc_cur = nullptr;    // [Nh+1][nf] complex: type-1 result before deconvolution, column-major
     void* d_tc_lag = nullptr;
-    void* d_td = nullptr;        // [nf][Nh+1] complex: type-2 coefficients (conjugated)
-    void* d_te = nullptr;        // [nf][nf/2+1] complex
+    void* d_td = nullptr;        // [Nh+1][nf] complex: type-2 coefficients (conjugated), column-major
+    void* d_te2 = nullptr;       // [Nh+1][nf] complex: their column transforms
+    void* d_te = nullptr;        // [nf][nf/2+1] complex: band rows of those, for the row transforms
     void* d_tf = nullptr;        // [nb][nf] real: type-2 grid in the band
     double* d_fac = nullptr;     // [Nh+1] (-1)^n h / psihat(n)
     float* d_facf = nullptr;     // the same in FP32 (mixed-path deconvolution)

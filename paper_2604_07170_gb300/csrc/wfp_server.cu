@@ -164,7 +164,7 @@ bool estimate_bytes(const Request& r, const wfp_opts& o, int64_t bytes[2], std::
     const bool keep = store && P.lag_active;  // the S history is stored only while the lag is in use
     b += modes * (8 + 4 + 32 + (keep ? P.L + P.W : P.W) * c + (rec ? P.W * c : 0));   // modes, state, S
     b += n_kappa * (4 * P.W * s + 24);                                                  // taps per |k|
-    b += nb * nf * s * (2 + rec) + nf * nh2 * c * (2 + rec) + nf * nc1 * c * (2 + rec); // grids
+    b += nb * nf * s * (2 + rec) + nf * nh2 * c * (2 + rec) + 2 * nf * nc1 * c * (2 + rec); // grids
     b += nf * nh2 * c;                                                                 // cuFFT work areas
     if (P.far_active) b += far * (8 + P.n_lambda * 16.0 + P.n_lambda * 8.0);            // far history
     b += r.Mt * (8 + 250 * 8.0);                                                       // self term (bound)

@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(256) k_modes(
     int2 nn = mode_n[m];
     int kid = mode_k[m];
     int row = nn.x < 0 ? nn.x + nf : nn.x;
-    int64_t gi = (int64_t)row * (Nh + 1) + nn.y;
+    int64_t gi = (int64_t)nn.y * nf + row;  // column-major pruned spectrum [Nh+1][nf]
     double f = fac[nn.x < 0 ? -nn.x : nn.x] * fac[nn.y];
     const int slot = (int)(n % R_cur);
     {
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(256) k_modes(
         td[gi] = o;
         if (nn.y == 0 && nn.x > 0) {
             o.y = (T)(af.y * cf);
-            td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
+            td[nf - nn.x] = o;  // column 0, row nf - n1
         }
         return;
     }
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(256) k_modes(
     td[gi] = o;
     if (nn.y == 0 && nn.x > 0) {
         o.y = (T)((an.y + af.y) * cf);
-        td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
+        td[nf - nn.x] = o;  // column 0, row nf - n1
     }
 }
 
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(256) k_modes_one(
     const int2 nn = mode_n[m];
     const int kid = mode_k[m];
     const int row = nn.x < 0 ? nn.x + nf : nn.x;
-    const int64_t gi = (int64_t)row * (Nh + 1) + nn.y;
+    const int64_t gi = (int64_t)nn.y * nf + row;  // column-major pruned spectrum [Nh+1][nf]
     const float f = facf[nn.x < 0 ? -nn.x : nn.x] * facf[nn.y];  // deconvolution, FP32 like the transform
     float2 s_cur, s_lag = make_float2(0.f, 0.f);
     {
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(256) k_modes_one(
         td[gi] = o;
         if (nn.y == 0 && nn.x > 0) {
             o.y = (float)af.y * cf;
-            td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
+            td[nf - nn.x] = o;  // column 0, row nf - n1
         }
         return;
     }
@@ -476,8 +476,39 @@ __global__ void __launch_bounds__(256) k_modes_one(
     td[gi] = o;
     if (nn.y == 0 && nn.x > 0) {
         o.y = (float)an.y * cf;
-        td[(int64_t)(nf - nn.x) * (Nh + 1)] = o;
+        td[nf - nn.x] = o;  // column 0, row nf - n1
     }
+}
+
+// ------------------------------------------------------------------------------ spectrum layout
+// The pruned spectrum is kept column-major, [Nh+1][nf] (column = the half-spectrum frequency of the
+// row transform, row = the full frequency of the column transform), so that the column transforms
+// run over contiguous vectors.  These move the band rows lb0..lb0+nb of the row transforms'
+// [nf][nf/2+1] layout into the kept columns of that layout and back, 32 x 32 tiles through shared
+// memory (block (32, 8), grid (ceil((Nh+1)/32), ceil(nb/32))).  Rows outside the band are never
+// written: the column transforms' input keeps its zeros there.
+template <typename C>
+__global__ void __launch_bounds__(256) k_band_to_cols(const C* __restrict__ src, C* __restrict__ dst, int nb, int nc1,
+                                                      int nh2, int nf, int lb0) {
+    __shared__ C tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x, ty = threadIdx.y;
+    for (int k = ty; k < 32; k += 8)
+        if (r0 + k < nb && c0 + tx < nc1) tile[k][tx] = src[(int64_t)(lb0 + r0 + k) * nh2 + c0 + tx];
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8)
+        if (r0 + tx < nb && c0 + k < nc1) dst[(int64_t)(c0 + k) * nf + lb0 + r0 + tx] = tile[tx][k];
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_cols_to_band(const C* __restrict__ src, C* __restrict__ dst, int nb, int nc1,
+                                                      int nh2, int nf, int lb0) {
+    __shared__ C tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x, ty = threadIdx.y;
+    for (int k = ty; k < 32; k += 8)
+        if (r0 + tx < nb && c0 + k < nc1) tile[k][tx] = src[(int64_t)(c0 + k) * nf + lb0 + r0 + tx];
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8)
+        if (r0 + k < nb && c0 + tx < nc1) dst[(int64_t)(lb0 + r0 + k) * nh2 + c0 + tx] = tile[tx][k];
 }
 
 // ------------------------------------------------------------------------------ far history
@@ -519,7 +550,7 @@ __global__ void __launch_bounds__(32 * kFarGroups) k_far(
             if (j == 0 && from_tc) {  // level n - L from this step's lagged transform
                 const int2 nn = mode_n[f];
                 const int row = nn.x < 0 ? nn.x + nf : nn.x;
-                const C t = tc_lag[(int64_t)row * (Nh + 1) + nn.y];
+                const C t = tc_lag[(int64_t)nn.y * nf + row];
                 if constexpr (sizeof(T) == 8) {
                     const double fd = fac[nn.x < 0 ? -nn.x : nn.x] * fac[nn.y];
                     v.x = (T)((double)t.x * fd);
@@ -757,19 +788,30 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err, cudaEvent_
             CK(cudaGetLastError());
         }
     }
-    // two-stage pruned FFT: rows of the band (R2C), then the kept columns (C2C, forward)
+    // two-stage pruned FFT: rows of the band (R2C), the kept columns into the column-major layout,
+    // then the columns (C2C, forward, contiguous)
     ProfScope psf(pl, PP_FFT1);
+    const dim3 tgrid((unsigned)((P.Nh + 1 + 31) / 32), (unsigned)((P.nb + 31) / 32)), tblk(32, 8);
     if (exec_r2c<T>(pl.fftA, (T*)pl.d_sp_cur, (C*)pl.d_tb_cur + (int64_t)P.lb0 * nh2) != WFP_OK) {
         err = "cufft type-1 row pass failed";
         return WFP_ECUDA;
     }
-    if (exec_c2c<T>(pl.fftB, (C*)pl.d_tb_cur, (C*)pl.d_tc_cur, CUFFT_FORWARD) != WFP_OK) {
+    k_band_to_cols<C><<<tgrid, tblk, 0, st>>>((const C*)pl.d_tb_cur, (C*)pl.d_tcol_cur, P.nb, P.Nh + 1, nh2, P.nf,
+                                              P.lb0);
+    CK(cudaGetLastError());
+    if (exec_c2c<T>(pl.fftB, (C*)pl.d_tcol_cur, (C*)pl.d_tc_cur, CUFFT_FORWARD) != WFP_OK) {
         err = "cufft type-1 column pass failed";
         return WFP_ECUDA;
     }
     if (lag_now && !pl.lag_store) {
-        if (exec_r2c<T>(pl.fftA, (T*)pl.d_sp_lag, (C*)pl.d_tb_lag + (int64_t)P.lb0 * nh2) != WFP_OK ||
-            exec_c2c<T>(pl.fftB, (C*)pl.d_tb_lag, (C*)pl.d_tc_lag, CUFFT_FORWARD) != WFP_OK) {
+        if (exec_r2c<T>(pl.fftA, (T*)pl.d_sp_lag, (C*)pl.d_tb_lag + (int64_t)P.lb0 * nh2) != WFP_OK) {
+            err = "cufft lagged type-1 failed";
+            return WFP_ECUDA;
+        }
+        k_band_to_cols<C><<<tgrid, tblk, 0, st>>>((const C*)pl.d_tb_lag, (C*)pl.d_tcol_lag, P.nb, P.Nh + 1, nh2,
+                                                  P.nf, P.lb0);
+        CK(cudaGetLastError());
+        if (exec_c2c<T>(pl.fftB, (C*)pl.d_tcol_lag, (C*)pl.d_tc_lag, CUFFT_FORWARD) != WFP_OK) {
             err = "cufft lagged type-1 failed";
             return WFP_ECUDA;
         }
@@ -806,10 +848,12 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err, cudaEvent_
     psm.stop();
     // type-2: columns (C2C, inverse) then band rows (C2R); the C2R input beyond column Nh is re-zeroed
     ProfScope ps2(pl, PP_FFT2);
-    if (exec_c2c<T>(pl.fftBi, (C*)pl.d_td, (C*)pl.d_te, CUFFT_INVERSE) != WFP_OK) {
+    if (exec_c2c<T>(pl.fftBi, (C*)pl.d_td, (C*)pl.d_te2, CUFFT_INVERSE) != WFP_OK) {
         err = "cufft type-2 column pass failed";
         return WFP_ECUDA;
     }
+    k_cols_to_band<C><<<tgrid, tblk, 0, st>>>((const C*)pl.d_te2, (C*)pl.d_te, P.nb, P.Nh + 1, nh2, P.nf, P.lb0);
+    CK(cudaGetLastError());
     if (nh2 > P.Nh + 1)
         CK(cudaMemset2DAsync((C*)pl.d_te + (int64_t)P.lb0 * nh2 + (P.Nh + 1), nh2 * sizeof(C), 0,
                              (nh2 - P.Nh - 1) * sizeof(C), P.nb, st));
