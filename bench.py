@@ -397,11 +397,13 @@ def source_hash(kernel: str = "local") -> str:
 
 def launches_per_step(info: dict, n_self: int) -> int:
     """Kernels of this library per step in the lagged regime (cuFFT's own kernels not counted):
-    ingest, local (two in the factored form), [self], combine, spread (x2 when the lag is recomputed),
-    modes, [far], interp, tick."""
+    ingest, local (two in the factored form), [self], combine, spread and the band-to-columns
+    transpose (x2 when the lag is recomputed), modes, [far], the columns-to-band transpose, interp,
+    tick."""
     spreads = 1 if info["lag_store"] else 2
     local = 2 if info.get("local_form") == 2 else 1
-    return 1 + local + (1 if n_self > 0 else 0) + 1 + spreads + 1 + (1 if info["far_active"] else 0) + 1 + 1
+    return (1 + local + (1 if n_self > 0 else 0) + 1 + 2 * spreads + 1 + (1 if info["far_active"] else 0) + 1 + 1
+            + 1)
 
 
 def drive(args):
