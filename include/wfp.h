@@ -101,9 +101,11 @@ enum { WFP_FP64 = 0, WFP_MIXED = 1 };
  *                 weights, factored, with a pair costing 8 bytes (16 in FP64) instead of a weight row;
  *                 pairs with r < dt keep stored rows.  The series is cut after the first coefficient
  *                 count (a multiple of 4) whose dropped tail is below the path's rounding (below 2^-25
- *                 of the interval's weight scale on the MIXED path; every coefficient on the FP64 path).
- *                 WFP_LOCAL_AUTO (0, default): FACTORED on the MIXED path, STORED on the FP64 path (where
- *                 the stored form needs fewer FP64 operations per pair).  FACTORED needs nmax <= 32.
+ *                 of the interval's weight scale on the MIXED path, rounded up to 16 or 32 for its
+ *                 kernels; every coefficient on the FP64 path); wfp_plan_get_info reports the count
+ *                 and wfp_debug_factored_table the table and the tail.  WFP_LOCAL_AUTO (0, default):
+ *                 FACTORED on the MIXED path, STORED on the FP64 path (where the stored form needs
+ *                 fewer FP64 operations per pair).  FACTORED needs nmax <= 32 and 8 (W - 1) M < 2^32.
  */
 typedef struct {
     int precision;
