@@ -164,6 +164,8 @@ static int signal_pieces(int fam, const double* p, piece_t* out) {
         return 3;
     }
     if (fam == 1) {
+        /* the switch-on 0.5 (erf(5 z) + 1) rises with derivative (5/sqrt(pi)) exp(-25 z^2), a Gaussian
+         * of standard deviation s = 1/(5 sqrt 2): the same cap min(period, 2 s) as the Gaussian pulses */
         double w = fabs(p[1]);
         double per = (w > 0) ? 2.0 * M_PI / w : 1e30;
         out[0].fam = 1;
@@ -171,7 +173,7 @@ static int signal_pieces(int fam, const double* p, piece_t* out) {
         out[0].q = -1;
         out[0].lo = 0.0;
         out[0].hi = 1e300;
-        out[0].scale = fmin(per, 0.4);
+        out[0].scale = fmin(per, 2.0 / (5.0 * sqrt(2.0)));
         return 1;
     }
     out[0].fam = fam;
