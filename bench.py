@@ -1,19 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the 2D TK-WFP per-step evaluation loop on GB300.
 
-Workload (default): 10^4 coincident sources/targets equispaced on 6 seeded random ellipses
-(semi-axes 2-8 wavelengths) in a 30x30-wavelength box, signals = sums of three
-Gaussian-enveloped sinusoids (carrier 2 pi rad per unit time), dt = 0.1 (~10 steps per
-period), N_t = 2000, tolerance 1e-6, FP64 path.  A "step" is one pass of the whole
-per-step loop (ingest, local part, self term, type-1 NUFFTs of the current and lagged
-levels, mode and far-history updates, type-2 NUFFT).  The timed window starts after
-L + W steps so that the lagged NUFFT and the far history are active.
+Default workload (the paper-scale case): 10^6 coincident sources/targets equispaced on 100
+seeded random ellipses (semi-axes 10-40 wavelengths) in a 300x300-wavelength box, signals =
+sums of three Gaussian-enveloped sinusoids (carrier 2 pi rad per unit time), dt = 0.1 (~10 steps
+per period), N_t = 3000, tolerance 1e-6, mixed-precision path; the FP64 path runs beside it on
+the same workload, and the 10^4-point workload (6 ellipses in a 30x30 box, N_t = 2000, timed in
+its lagged / far-history regime) is reported as a sub-record on both paths.  A "step" is one pass
+of the whole per-step loop (ingest, local part, self term, type-1 NUFFT(s), mode and far-history
+updates, type-2 NUFFT).  The timed window ends at a step where the field is well developed.
 
-Metric: target-updates/s = (targets x timed steps) / time.  `value` is device-timed with
-CUDA events on the plan's stream, inputs resident in HBM; `e2e` is measured through the
-C ABI with host buffers (host->device copy of sigma_n and device->host copy of u_n inside
-the timed region).  `--impl reference` times the FP64 CPU oracle (exact retarded field)
-on the host cores on a bounded sample of the same workload.
+Metric: target-updates/s = (targets x timed steps) / time.  `value` is device-timed with CUDA
+events on the plan's stream, inputs resident in HBM; `e2e` is measured through the C ABI with
+host buffers (host->device copy of sigma_n and device->host copy of u_n inside the timed region).
+Accuracy: relative L2 error against the FP64 CPU oracle (exact retarded field) on random targets
+at two timed steps.  `--impl reference` times that oracle on the host cores on a bounded sample
+of the same workload.
 """
 from __future__ import annotations
 
@@ -31,33 +33,40 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "target-updates/s (M_t x N_t per second), FP64 path, rel L2 <= 1e-6 per step"
-FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 2 FP64 FMA per clock per SM at the maximum SM clock
-FP32_PEAK_TFLOPS = 152 * 2.07e9 * 256 / 1e12  # 128 FP32 FMA per clock per SM
+METRIC = "M*N_t target-updates/s (targets x steps per second), mixed-precision path; FP64 path beside"
+# unit counts x the maximum SM clock; used only when the measured FMA-loop peak is unavailable
+FP64_PEAK_DERIVED = 152 * 2.07e9 * 4 / 1e12    # 2 FP64 FMA per clock per SM
+FP32_PEAK_DERIVED = 152 * 2.07e9 * 256 / 1e12  # 128 FP32 FMA per clock per SM
+# the step at which the timed window ends, per workload: one where the field is developed (the
+# pulses start near t = 8); workloads with a lagged regime are timed after it instead
+TIMED_END = {"cfg1": 90, "cfg4": 400}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cfg2")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variant")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    ap.add_argument("--profile-steps", type=int, default=100)
-    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--config", default="cfg4")
+    ap.add_argument("--nt", type=int, default=0, help="override the workload's N_t (e.g. to stay before the lag)")
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-beside", action="store_true", help="skip the other path on the same workload")
+    ap.add_argument("--sub", default="cfg2", help="workload of the sub-record ('' for none)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline and accuracy")
+    ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--opt", action="append", default=[], help="plan option key=value (wfp_opts field)")
     ap.add_argument("--drive", type=int, default=0,
                     help="only step the workload this many times with graphs off and exit (profiler target)")
     ap.add_argument("--serve", type=int, default=0,
                     help="serving benchmark with this many requests (Poisson arrivals) instead of the step loop")
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered load as a fraction of batch capacity")
+    ap.add_argument("--serve-check", type=int, default=5, help="requests checked against the oracle (--serve)")
     ap.add_argument("--max-active", type=int, default=48)
-    ap.add_argument("--accuracy-targets", type=int, default=16,
-                    help="random targets compared with the oracle at the last timed step")
-    a = ap.parse_args()
+    ap.add_argument("--accuracy-targets", type=int, default=100,
+                    help="random targets compared with the oracle at two timed steps")
+    a = ap.parse_args(argv)
     a.plan_opts = {}
     for kv in a.opt:
         k, v = kv.split("=")
@@ -101,7 +110,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -142,13 +151,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+_ALU = {}  # measured FMA-loop peaks of this GPU, filled once per run (TFLOP/s)
+
+
+def measure_alu_peaks() -> None:
+    """FP64 and FP32 FMA throughput of this GPU (wfp_debug_alu_peak: a timed loop of independent FMAs)."""
+    from paper_2604_07170_gb300 import wfp
+    for fp64 in (True, False):
+        tf, _ = wfp.alu_peak(fp64)
+        _ALU["fp64" if fp64 else "fp32"] = tf
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    out = {"hbm_gbs": 6800.0, "source": "fallback"}
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
-    return {"hbm_gbs": 6800.0, "source": "fallback"}
+        out = {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    if "fp64" in _ALU:
+        out.update(fp64_tflops=_ALU["fp64"], fp32_tflops=_ALU["fp32"],
+                   alu_source="measured: FMA loop on this GPU (wfp_debug_alu_peak)")
+    else:
+        out.update(fp64_tflops=FP64_PEAK_DERIVED, fp32_tflops=FP32_PEAK_DERIVED,
+                   alu_source="derived: 152 SMs x 2070 MHz x FMA units per SM")
+    return out
 
 
 def part_model(info: dict, M: int, Mt: int, fp64: bool) -> dict:
@@ -164,6 +191,10 @@ def part_model(info: dict, M: int, Mt: int, fp64: bool) -> dict:
     lag = 1 if info["lag_active"] else 0  # the timed window is in the lagged regime when there is one
     spreads = 1 + (lag and not info["lag_store"])  # a second (lagged) spread only without the stored S history
     tapw = 4 * W * s if fp64 else 8 * W * 4     # FIR taps per |k|: FP64, or FP32 hi/lo pairs
+    # the part of the [nb][nf] band that spreading writes and interpolation reads: the non-empty tiles
+    # (the whole band when the tile count is unknown)
+    ts = info.get("spread_tile") or 0
+    band = min(nb * nfg, info["n_spread_tiles"] * ts * ts) if info.get("n_spread_tiles") and ts else nb * nfg
     m = {}
     if info.get("local_form") == 2:
         # factored form: pair records (8 bytes, 16 in FP64), near pairs' stored rows, the per-step
@@ -181,12 +212,12 @@ def part_model(info: dict, M: int, Mt: int, fp64: bool) -> dict:
     m["self"] = (nself * (nsoe * 16 + W * s + 12), nself * (nsoe * 4 + 2 * W))
     m["ingest"] = (M * (8 + 4 + 2 * s + (2 * NW * s if NW == 32 else 0)), 0)
     m["combine"] = (Mt * (4 + 4 * 8), Mt * 2)
-    m["spread"] = (spreads * (nb * nb * s + M * (2 * w * s + 4 + s)), spreads * 2 * M * w * w)
+    m["spread"] = (spreads * (band * s + M * (2 * w * s + 4 + s)), spreads * 2 * M * w * w)
     # S read and ring write, W ring levels (current and lagged), alpha/alphadot read+write, grid write
     m["modes"] = (nm * ((1 + lag) * W * c + 2 * c + 4 * 16 + 12 + c) + nk * tapw, nm * (8 * W * (1 + lag) + 16))
     # E_l read+write (FP64 complex) and H_l per term, W lagged levels, grid read+write
     m["far"] = (nf_ * (nl * (32 + 8) + W * c + 2 * c), nf_ * (nl * 8 + 4 * W))
-    m["interp"] = (nb * nb * s + Mt * (2 * w * s + 4 + 8), 2 * Mt * w * w)
+    m["interp"] = (band * s + Mt * (2 * w * s + 4 + 8), 2 * Mt * w * w)
     # two-stage pruned FFTs: R2C over the nb band rows, C2C over the N_h + 1 kept columns (and back)
     nh2, nc1, lg = nfg // 2 + 1, info["Nh"] + 1, math.log2(nfg)
     fft_b = nb * nfg * s + nb * nh2 * c + 2 * nb * nc1 * c + 2 * nfg * nc1 * c  # rows, band transpose, columns
@@ -197,92 +228,85 @@ def part_model(info: dict, M: int, Mt: int, fp64: bool) -> dict:
 
 
 # ----------------------------------------------------------------------------- our arm
-def run_ours(args, rank: int, world: int, dist):
+def measure(wl, precision: str, K: int, Wm: int, e2e_steps: int, prof_steps: int, keep: int, dev, dist,
+            plan_opts: dict, timed_end: int = 0) -> dict:
+    """Plan the workload, step it to the timed window, time K steps (CUDA events on the plan's
+    stream, inputs resident), keep the outputs of the last `keep` timed steps, then per-part event
+    timing and the end-to-end rate through the C ABI with host buffers."""
     import torch
-    from paper_2604_07170_gb300 import inputs, wfp
+    from paper_2604_07170_gb300 import wfp
+    M, Mt = wl.M, wl.M
+    prec = 0 if precision == "fp64" else 1
+    stream = torch.cuda.Stream(device=dev)
+    p0 = wfp.select_params(wl.meta["box"] / 2, wl.dt, wl.n_steps, wl.band_limit, wl.tol, precision=prec)
+    # every part the workload uses is active in the timed window: after the lag switches on when the
+    # workload has a lagged regime (N_t > L), else once the local window is full and the field developed
+    pre = p0["L"] + p0["W"] + 1 if p0["lag_active"] else p0["nmax"] + 1
+    first = max(pre + Wm + 1, timed_end - K + 1)
+    Nt = max(wl.n_steps, first + K - 1 + prof_steps + e2e_steps)
+    t0 = time.perf_counter()
+    plan = wfp.Plan(wl.src_xy, None, wl.dt, Nt, wl.band_limit, wl.tol, precision=prec, stream=stream.cuda_stream,
+                    **plan_opts)
+    plan_s = time.perf_counter() - t0
+    info = plan.info()
+    out = torch.empty(Mt, dtype=torch.float64, device=dev)
+    n = 0
+    chunk = 256
 
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
-    torch.cuda.set_device(dev)
-    wl = inputs.make(args.config, seed_offset=rank)
-    M = Mt = wl.M
-    res = {}
-
-    def one(precision: str, K: int, Wm: int, timed_e2e: bool, prof_steps: int):
-        stream = torch.cuda.Stream(device=dev)
-        plan0 = wfp.select_params(wl.meta["box"] / 2, wl.dt, wl.n_steps, wl.band_limit, wl.tol,
-                                  precision=0 if precision == "fp64" else 1)
-        # reach the lagged / far-history regime when the workload has one (N_t > L); otherwise only fill
-        # the local window, so that every part the workload uses is active in the timed region
-        pre = plan0["L"] + plan0["W"] + 1 if plan0["lag_active"] else plan0["nmax"] + 1
-        e2e_steps = args.e2e_steps if timed_e2e else 0
-        Nt = max(wl.n_steps, pre + Wm + K + prof_steps + e2e_steps)
-        t0 = time.perf_counter()
-        plan = wfp.Plan(wl.src_xy, None, wl.dt, Nt, wl.band_limit, wl.tol,
-                        precision=0 if precision == "fp64" else 1, stream=stream.cuda_stream, **args.plan_opts)
-        plan_s = time.perf_counter() - t0
-        info = plan.info()
-        out = torch.empty(Mt, dtype=torch.float64, device=dev)
-        n = 0
-        chunk = 256
-
-        def run_device(nsteps):
-            nonlocal n
-            done = 0
-            while done < nsteps:
-                k = min(chunk, nsteps - done)
-                sig = torch.from_numpy(wl.sigma(n + 1, n + 1 + k)).to(dev)
-                torch.cuda.synchronize(dev)
-                for i in range(k):
-                    plan.step(sig[i], out)
-                n += k
-                done += k
-
-        run_device(pre + Wm)
-        # timed region: inputs already resident in HBM
-        sig = torch.from_numpy(wl.sigma(n + 1, n + 1 + K)).to(dev)
-        torch.cuda.synchronize(dev)
-        if dist:
-            dist.barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(dev.index) as clk:
+    def run_device(nsteps):
+        nonlocal n
+        done = 0
+        while done < nsteps:
+            k = min(chunk, nsteps - done)
+            sig = torch.from_numpy(wl.sigma(n + 1, n + 1 + k)).to(dev)
             torch.cuda.synchronize(dev)
-            e0.record(stream)
-            for i in range(K):
+            for i in range(k):
                 plan.step(sig[i], out)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-        n += K
-        ms = e0.elapsed_time(e1)
-        ms = max_over_ranks(dist, ms, dev)
-        r = {"ms": ms, "K": K, "info": info, "plan_s": plan_s, "clocks": clk.summary(), "u_last": out.cpu().numpy(),
-             "n_last": n, "workload": args.config}
-        # per-part timing with CUDA events on the plan's stream
-        if prof_steps > 0:
-            plan.profile(True)
-            run_device(prof_steps)
-            r["parts"] = plan.profile_read()
-            r["prof_steps"] = prof_steps
-            plan.profile(False)
-        # end to end through the C ABI with host buffers
-        if e2e_steps > 0:
-            sig_h = wl.sigma(n + 1, n + 1 + e2e_steps)
-            u_h = np.empty(Mt)
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            for i in range(e2e_steps):
-                plan.step(sig_h[i], u_h)
-            torch.cuda.synchronize(dev)
-            r["e2e_s"] = time.perf_counter() - t0
-            r["e2e_steps"] = e2e_steps
-            n += e2e_steps
-        plan.close()
-        return r
+            n += k
+            done += k
 
-    prec = args.precision
-    res["main"] = one(prec, args.steps, args.warmup, True, args.profile_steps)
-    if not args.no_mixed and prec == "fp64":
-        res["mixed"] = one("mixed", min(args.steps, 500), args.warmup, False, args.profile_steps)
-    return wl, res
+    run_device(first - 1)
+    # timed region: inputs already resident in HBM; the last `keep` steps write their own buffers
+    sig = torch.from_numpy(wl.sigma(n + 1, n + 1 + K)).to(dev)
+    kept = torch.empty((keep, Mt), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for i in range(K):
+            plan.step(sig[i], kept[i - (K - keep)] if i >= K - keep else out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(dist, ms, dev)
+    r = {"ms": ms, "K": K, "info": info, "plan_s": plan_s, "clocks": clk.summary(), "precision": precision,
+         "kept": kept.cpu().numpy(), "kept_steps": list(range(n + K - keep + 1, n + K + 1)), "n_last": n + K,
+         "workload": wl.name}
+    n += K
+    if prof_steps > 0:  # per-part timing with CUDA events on the plan's stream (parts in sequence)
+        plan.profile(True)
+        run_device(prof_steps)
+        r["parts"] = plan.profile_read()
+        r["prof_steps"] = prof_steps
+        plan.profile(False)
+    if e2e_steps > 0:  # end to end through the C ABI with host buffers
+        sig_h = wl.sigma(n + 1, n + 1 + e2e_steps)
+        u_h = np.empty(Mt)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            plan.step(sig_h[i], u_h)
+        torch.cuda.synchronize(dev)
+        r["e2e_s"] = time.perf_counter() - t0
+        r["e2e_steps"] = e2e_steps
+        n += e2e_steps
+    plan.close()
+    del plan
+    torch.cuda.synchronize(dev)
+    return r
 
 
 def cpu_oracle_rate(wl, n_eval_hint: int, t_budget: float, step: int):
@@ -302,18 +326,29 @@ def cpu_oracle_rate(wl, n_eval_hint: int, t_budget: float, step: int):
         n = int(min(n_eval_hint, max(2 * n, n * 0.5 * t_budget / max(dt, 1e-3))))
 
 
-def accuracy_sample(wl, u, n_step, k=16):
+def oracle_reference(wl, steps, k: int, seed: int = 1):
+    """The oracle's field at k random targets (seeded) at each of `steps`: (indices, array [steps][k])."""
     import oracle
-    rng = np.random.default_rng(1)
-    idx = rng.choice(wl.M, k, replace=False)
-    ev = np.column_stack([wl.src_xy[idx], np.full(k, n_step * wl.dt)])
-    ref = oracle.field(wl.src_xy, wl.params, ev, r_coinc=1e-12 * wl.meta["box"])
-    return float(np.linalg.norm(u[idx] - ref) / np.linalg.norm(ref))
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(wl.M, min(k, wl.M), replace=False)
+    ev = np.array([[wl.src_xy[i, 0], wl.src_xy[i, 1], n * wl.dt] for n in steps for i in idx])
+    ref = oracle.field(wl.src_xy, wl.params, ev, r_coinc=1e-12 * wl.meta["box"]).reshape(len(steps), -1)
+    return idx, ref
+
+
+def accuracy(r: dict, idx, ref) -> dict:
+    """Relative L2 error per kept step on the sampled targets, and the relative max-norm error."""
+    got = r["kept"][:, idx]
+    l2 = [float(np.linalg.norm(g - f) / np.linalg.norm(f)) for g, f in zip(got, ref)]
+    mx = [float(np.max(np.abs(g - f)) / np.max(np.abs(f))) for g, f in zip(got, ref)]
+    return {"rel_l2_vs_oracle": max(l2), "per_step": dict(zip(map(str, r["kept_steps"]), l2)),
+            "rel_max_vs_oracle": max(mx), "targets": int(len(idx)), "steps": r["kept_steps"]}
 
 
 def roofline(r: dict, M: int, Mt: int, fp64: bool) -> tuple[dict, dict]:
     peaks = measured_peaks()
     model = part_model(r["info"], M, Mt, fp64)
+    alu_peak = peaks["fp64_tflops"] if fp64 else peaks["fp32_tflops"]
     parts = r.get("parts", {})
     per = {}
     for name, (ms, cnt) in parts.items():
@@ -325,7 +360,6 @@ def roofline(r: dict, M: int, Mt: int, fp64: bool) -> tuple[dict, dict]:
             t = ms / cnt * 1e-3
             e["GB/s"] = b / t / 1e9
             e["TFLOP/s"] = f / t / 1e12
-            alu_peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
             tb, tf = b / (peaks["hbm_gbs"] * 1e9), f / (alu_peak * 1e12)
             e["bound"] = "hbm" if tb >= tf else "alu"
         per[name] = e
@@ -354,19 +388,18 @@ def roofline(r: dict, M: int, Mt: int, fp64: bool) -> tuple[dict, dict]:
                     "unit": "GB/s", "frac": round(e["GB/s"] / peaks["hbm_gbs"], 4), "traffic": traffic,
                     "peak_source": peaks["source"]}
         else:
-            pk = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
-            roof = {"kernel": dom, "bound": "alu", "achieved": round(e["TFLOP/s"], 4), "peak": round(pk, 3),
-                    "unit": "TFLOP/s", "frac": round(e["TFLOP/s"] / pk, 4), "traffic": traffic,
-                    "peak_source": "derived: 152 SMs x 2070 MHz x " + ("4 FP64" if fp64 else "256 FP32") + " flop/clk"}
+            roof = {"kernel": dom, "bound": "alu", "achieved": round(e["TFLOP/s"], 4), "peak": round(alu_peak, 3),
+                    "unit": "TFLOP/s", "frac": round(e["TFLOP/s"] / alu_peak, 4), "traffic": traffic,
+                    "peak_source": peaks["alu_source"] + (" FP64" if fp64 else " FP32")}
     return roof, per
 
 
 def parts_roofline(per: dict, fp64: bool) -> dict:
     """Each timed part against its own bound (algorithmic bytes / flops per launch over its
     event-timed launch, in sequence): HBM against the measured copy bandwidth, ALU against the
-    derived FP64 (FP64 path) or FP32 peak."""
+    FP64 (FP64 path) or FP32 FMA peak."""
     peaks = measured_peaks()
-    alu = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+    alu = peaks["fp64_tflops"] if fp64 else peaks["fp32_tflops"]
     out = {}
     for k, e in per.items():
         if "bound" not in e:
@@ -396,14 +429,45 @@ def source_hash(kernel: str = "local") -> str:
 
 
 def launches_per_step(info: dict, n_self: int) -> int:
-    """Kernels of this library per step in the lagged regime (cuFFT's own kernels not counted):
-    ingest, local (two in the factored form), [self], combine, spread and the band-to-columns
-    transpose (x2 when the lag is recomputed), modes, [far], the columns-to-band transpose, interp,
-    tick."""
-    spreads = 1 if info["lag_store"] else 2
+    """Kernels of this library per step (cuFFT's own kernels not counted): ingest, local (two in the
+    factored form), [self], combine, spread and the band-to-columns transpose (x2 when the lag is
+    recomputed), modes, [far], the columns-to-band transpose, interp, tick."""
+    lag = bool(info["lag_active"])
+    spreads = 2 if (lag and not info["lag_store"]) else 1
     local = 2 if info.get("local_form") == 2 else 1
-    return (1 + local + (1 if n_self > 0 else 0) + 1 + 2 * spreads + 1 + (1 if info["far_active"] else 0) + 1 + 1
-            + 1)
+    far = 1 if (lag and info["far_active"]) else 0
+    return 1 + local + (1 if n_self > 0 else 0) + 1 + 2 * spreads + 1 + far + 1 + 1 + 1
+
+
+def footprint(info: dict) -> dict:
+    return {"device_bytes": info["device_bytes"], "local_part": info["bytes_local"], "grid": info["bytes_grid"],
+            "history_state": info["bytes_history"], "fft_work": info["bytes_fft_work"]}
+
+
+def path_record(r: dict, wl, world: int, fp64: bool) -> dict:
+    """The figures of one timed path: rate, step time, rooflines, part times, footprint, e2e."""
+    roof, parts = roofline(r, wl.M, wl.M, fp64)
+    fft_ms = sum(parts.get(k, {}).get("ms_per_launch", 0) * parts.get(k, {}).get("launches", 0)
+                 for k in ("fft_type1", "fft_type2"))
+    tot_ms = sum(v["ms_per_launch"] * v["launches"] for v in parts.values())
+    info = r["info"]
+    rec = {"value": world * wl.M * r["K"] / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / r["K"],
+           "timed_steps": [r["n_last"] - r["K"] + 1, r["n_last"]], "roofline": roof,
+           "fft_time_share": round(fft_ms / tot_ms, 4) if tot_ms else None,
+           "parts_ms_per_step": {k: round(v["ms_per_launch"] * v["launches"] / r["prof_steps"], 5)
+                                 for k, v in parts.items()} if "prof_steps" in r else {},
+           "parts_roofline": parts_roofline(parts, fp64), "footprint": footprint(info),
+           "plan_seconds": round(r["plan_s"], 3), "clocks": r["clocks"],
+           "gpu_launches": r["K"] * launches_per_step(info, info["n_self"])}
+    if "e2e_s" in r:
+        rec["e2e"] = {"value": wl.M * r["e2e_steps"] / r["e2e_s"], "unit": "target-updates/s",
+                      "h2d_bytes_per_step": wl.M * 8, "d2h_bytes_per_step": wl.M * 8, "steps": r["e2e_steps"]}
+    return rec
+
+
+def workload_label(wl, precision: str) -> str:
+    return (f"{wl.name}: M={wl.M} coincident sources/targets on ellipses in a {wl.meta['box']:g}x"
+            f"{wl.meta['box']:g}-wavelength box, dt={wl.dt}, N_t={wl.n_steps}, tol={wl.tol:g}, {precision}")
 
 
 def drive(args):
@@ -411,9 +475,11 @@ def drive(args):
     profiler sees every kernel as its own launch.  Prints nothing but a completion line."""
     from paper_2604_07170_gb300 import inputs, wfp
     wl = inputs.make(args.config)
+    if args.nt:
+        wl.n_steps = args.nt
     opts = dict(args.plan_opts)
     opts.setdefault("use_graph", 0)
-    plan = wfp.Plan(wl.src_xy, None, wl.dt, max(wl.n_steps, args.drive), wl.band_limit, wl.tol,
+    plan = wfp.Plan(wl.src_xy, None, wl.dt, wl.n_steps if args.nt else max(wl.n_steps, args.drive), wl.band_limit, wl.tol,
                     precision=0 if args.precision == "fp64" else 1, **opts)
     u = np.empty(wl.M)
     for n0 in range(0, args.drive, 256):
@@ -491,8 +557,8 @@ def serve(args):
     print(json.dumps(line))
 
 
-def main():
-    args = parse()
+def main(argv=None):
+    args = parse(argv)
     if args.drive:
         return drive(args)
     if args.serve:
@@ -503,98 +569,121 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    wl, res = run_ours(args, rank, world, dist)
+    import torch
+    from paper_2604_07170_gb300 import inputs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    measure_alu_peaks()
+    wl = inputs.make(args.config, seed_offset=rank)
+    K, Wm = args.steps, args.warmup
+    keep = min(2, K)
+    tend = TIMED_END.get(args.config, 0)
+    fp64 = args.precision == "fp64"
+    r = measure(wl, args.precision, K, Wm, args.e2e_steps, args.profile_steps, keep, dev, dist, args.plan_opts, tend)
+    other = "mixed" if fp64 else "fp64"
+    rb = None
+    if not args.no_beside:
+        rb = measure(wl, other, K, Wm, min(args.e2e_steps, 20), min(args.profile_steps, 10), keep, dev, dist,
+                     args.plan_opts, tend)
+    subs = {}
+    wl2 = None
+    if args.sub and args.sub != args.config:
+        wl2 = inputs.make(args.sub, seed_offset=rank)
+        for prec in ("fp64", "mixed"):
+            subs[prec] = measure(wl2, prec, max(K, 200), Wm, 0, 50, keep, dev, dist, args.plan_opts,
+                                 TIMED_END.get(args.sub, 0))
     if rank != 0:
         return
-    r = res["main"]
-    fp64 = args.precision == "fp64"
-    K = r["K"]
-    value = world * wl.M * K / (r["ms"] * 1e-3)
-    roof, parts = roofline(r, wl.M, wl.M, fp64)
-    fft_ms = sum(parts.get(k, {}).get("ms_per_launch", 0) * parts.get(k, {}).get("launches", 0)
-                 for k in ("fft_type1", "fft_type2"))
-    tot_ms = sum(v["ms_per_launch"] * v["launches"] for v in parts.values())
+    rec = path_record(r, wl, world, fp64)
     info = r["info"]
     line = {
         "metric": METRIC,
-        "value": value,
+        "value": rec["value"],
         "unit": "target-updates/s",
         "n_gpus": world,
         "steps": K,
-        "warmup": args.warmup,
-        "ms_per_step": r["ms"] / K,
+        "warmup": Wm,
+        "ms_per_step": rec["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if fp64 else "f64-state/f32",
+        "dtype": "f64" if fp64 else "f32+f64 (mixed)",
         "data": "synthetic (seeded ellipse geometry, Gaussian-sinusoid signals)",
-        "config": {"workload": f"{args.config}: M={wl.M} coincident sources/targets on ellipses in a "
-                               f"{wl.meta['box']:g}x{wl.meta['box']:g}-wavelength box, dt={wl.dt}, N_t={wl.n_steps}, "
-                               f"tol={wl.tol:g}, {args.precision}",
-                   "timed_steps": [r["n_last"] - K + 1, r["n_last"]],
+        "config": {"workload": workload_label(wl, args.precision),
+                   "timed_steps": rec["timed_steps"],
                    "l2": "inputs larger than L2 (%.2f GB of algorithmic bytes per step across the parts)" % (
                        sum(v["bytes"] for v in part_model(info, wl.M, wl.M, fp64).values()) / 1e9),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "W": info["W"], "p": info["p"], "L": info["L"], "N_modes_half": info["n_modes"],
-                   "nf": info["nf"], "n_pairs": info["n_pairs"], "n_lambda": info["n_lambda"],
-                   "plan_seconds": round(r["plan_s"], 3), "device_bytes": info["device_bytes"],
+                   "nf": info["nf"], "nb": info["nb"], "n_pairs": info["n_pairs"], "n_lambda": info["n_lambda"],
+                   "plan_seconds": rec["plan_seconds"], "footprint": rec["footprint"],
                    "upsampfac": round(info["upsampfac"], 4), "kernel_width": info["kernel_width"],
-                   "lag_store": info["lag_store"], "local_variant": info["local_variant"],
-                   "spread_tile": info["spread_tile"], "spread_chunk": info["spread_chunk"],
-                   "plan_opts": args.plan_opts},
-        "clocks": r["clocks"],
-        "gpu_launches": K * launches_per_step(info, info["n_self"]),
-        "roofline": roof,
-        "fft_time_share": round(fft_ms / tot_ms, 4) if tot_ms else None,
-        "parts_ms_per_step": {k: round(v["ms_per_launch"] * v["launches"] / r["prof_steps"], 5)
-                              for k, v in parts.items()},
-        "parts_roofline": parts_roofline(parts, fp64),
+                   "lag_active": info["lag_active"], "lag_store": info["lag_store"],
+                   "local_form": info["local_form"], "local_nc": info["local_nc"],
+                   "local_variant": info["local_variant"], "spread_tile": info["spread_tile"],
+                   "spread_chunk": info["spread_chunk"], "plan_opts": args.plan_opts},
+        "clocks": rec["clocks"],
+        "gpu_launches": rec["gpu_launches"],
+        "roofline": rec["roofline"],
+        "fft_time_share": rec["fft_time_share"],
+        "parts_ms_per_step": rec["parts_ms_per_step"],
+        "parts_roofline": rec["parts_roofline"],
+        "alu_peaks_tflops": {"fp64": round(_ALU.get("fp64", 0.0), 4), "fp32": round(_ALU.get("fp32", 0.0), 3),
+                             "source": measured_peaks()["alu_source"]},
     }
-    if "e2e_s" in r:
-        line["e2e"] = {"value": wl.M * r["e2e_steps"] / r["e2e_s"], "unit": "target-updates/s",
-                       "h2d_bytes_per_step": wl.M * 8, "d2h_bytes_per_step": wl.M * 8}
-    if "mixed" in res:
-        m = res["mixed"]
-        roof_m, parts_m = roofline(m, wl.M, wl.M, False)
-        line["mixed"] = {"value": world * wl.M * m["K"] / (m["ms"] * 1e-3), "ms_per_step": m["ms"] / m["K"],
-                         "roofline": roof_m, "parts_roofline": parts_roofline(parts_m, False),
-                         "parts_ms_per_step": {k: round(v["ms_per_launch"] * v["launches"] / m["prof_steps"], 5)
-                                               for k, v in parts_m.items()}}
+    if "e2e" in rec:
+        line["e2e"] = rec["e2e"]
+    if rb is not None:
+        line[other] = path_record(rb, wl, world, not fp64)
+        line[other]["speedup_of_" + args.precision] = (line["value"] / line[other]["value"] if not fp64
+                                                      else line[other]["value"] / line["value"])
+    if subs:
+        line["sub"] = {"workload": workload_label(wl2, "fp64 and mixed")}
+        for prec, rs in subs.items():
+            line["sub"][prec] = path_record(rs, wl2, world, prec == "fp64")
     if not args.no_cpu:
         try:
-            rate, cores, n_ev, dt = cpu_oracle_rate(wl, 512, 20.0, r["n_last"])
+            rate, cores, n_ev, dt = cpu_oracle_rate(wl, 4096, 20.0, r["n_last"])
             line["cpu_baseline"] = {"value": rate, "unit": "target-updates/s", "cores": cores, "kind": "oracle",
-                                    "sample": f"{n_ev} random targets of {args.config} at one timed step "
+                                    "sample": f"{n_ev} random targets of {args.config} at step {r['n_last']} "
                                               f"(exact retarded field by quadrature), {dt:.1f} s"}
-            k = min(args.accuracy_targets, wl.M)
-            line["accuracy"] = {"rel_l2_vs_oracle": accuracy_sample(wl, r["u_last"], r["n_last"], k),
-                                "sample": f"{k} random targets at step {r['n_last']}"}
-            if "mixed" in res:
-                line["mixed"]["rel_l2_vs_oracle"] = accuracy_sample(wl, res["mixed"]["u_last"],
-                                                                    res["mixed"]["n_last"], k)
+            idx, ref = oracle_reference(wl, r["kept_steps"], args.accuracy_targets)
+            line["accuracy"] = accuracy(r, idx, ref)
+            if rb is not None:
+                if rb["kept_steps"] != r["kept_steps"]:
+                    idx, ref = oracle_reference(wl, rb["kept_steps"], args.accuracy_targets)
+                line[other]["accuracy"] = accuracy(rb, idx, ref)
+            for prec, rs in subs.items():
+                i2, ref2 = oracle_reference(wl2, rs["kept_steps"], args.accuracy_targets)
+                line["sub"][prec]["accuracy"] = accuracy(rs, i2, ref2)
         except Exception as e:  # pragma: no cover
             line["cpu_baseline"] = {"error": str(e)}
     print(json.dumps(line))
 
 
 def run_reference(args, rank, world, dist):
-    """The FP64 CPU oracle as the reference arm, rank 0 only."""
+    """The FP64 CPU oracle as the reference arm, rank 0 only: the same workload, at the steps our
+    arm times, on a bounded sample of targets per step."""
     if rank != 0:
         return
     import oracle
     from paper_2604_07170_gb300 import inputs
     wl = inputs.make(args.config)
     cores = oracle.num_threads()
+    if args.config in TIMED_END:  # the window our arm times
+        last = TIMED_END[args.config]
+        steps = np.clip(np.arange(last - args.steps - args.warmup + 1, last + 1), 1, wl.n_steps)
+    else:  # workloads timed in their lagged regime: steps spread over the second half of the run
+        steps = np.linspace(wl.n_steps // 2, wl.n_steps, args.steps + args.warmup).astype(int)
     # size each step's sample so that warmup + steps stay within ~2 minutes
     rng = np.random.default_rng(0)
     probe = max(cores, 8)
     idx = rng.choice(wl.M, probe, replace=False)
-    ev = np.column_stack([wl.src_xy[idx], np.full(probe, min(900, wl.n_steps) * wl.dt)])
+    ev = np.column_stack([wl.src_xy[idx], np.full(probe, steps[-1] * wl.dt)])
     t0 = time.perf_counter()
     oracle.field(wl.src_xy, wl.params, ev, r_coinc=1e-12 * wl.meta["box"])
     per_eval = (time.perf_counter() - t0) / probe
-    S = int(max(1, min(wl.M, 120.0 / max(1, args.steps + args.warmup) / per_eval)))
-    steps = np.linspace(min(800, wl.n_steps // 2), wl.n_steps, args.steps + args.warmup).astype(int)
+    S = int(max(1, min(wl.M, 120.0 / len(steps) / per_eval)))
     tot_t, tot_n = 0.0, 0
     for i, n in enumerate(steps):
         idx = rng.choice(wl.M, S, replace=False)
@@ -605,13 +694,12 @@ def run_reference(args, rank, world, dist):
             tot_t += time.perf_counter() - t0
             tot_n += S
     value = tot_n / tot_t
-    sample = f"{S} random targets per step over {args.steps} steps of {args.config}"
+    sample = f"{S} random targets per step over steps {int(steps[args.warmup])}..{int(steps[-1])} of {args.config}"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "target-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded ellipse geometry, Gaussian-sinusoid signals)",
-            "config": {"workload": f"{args.config}: M={wl.M}, box {wl.meta['box']:g}, dt={wl.dt}, "
-                                   f"N_t={wl.n_steps}, tol={wl.tol:g}, fp64 (CPU oracle)"},
+            "config": {"workload": workload_label(wl, "fp64 (CPU oracle)")},
             "cpu_baseline": {"value": value, "unit": "target-updates/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "target-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

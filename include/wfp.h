@@ -166,6 +166,14 @@ typedef struct {
     int local_form;                  /* WFP_LOCAL_STORED or WFP_LOCAL_FACTORED, as built */
     int local_nc;                    /* Chebyshev coefficients per interval (factored form), else 0 */
     int64_t n_near_pairs;            /* pairs with r < dt (stored weight rows in the factored form) */
+    int64_t n_spread_tiles;          /* non-empty spread_tile x spread_tile tiles of the fine-grid band
+                                        (the part of the band that spreading writes and interpolation reads) */
+    int64_t bytes_local;             /* device_bytes held by the local part (pair lists, weight rows or
+                                        factored records, series table and the per-step contraction) */
+    int64_t bytes_grid;              /* ... by the NUFFT fine-grid band and the pruned spectra */
+    int64_t bytes_history;           /* ... by the carried state: signal windows and history, mode amplitudes
+                                        alpha and alpha-dot, the S levels, far and self recurrence states */
+    int64_t bytes_fft_work;          /* cuFFT work areas (held by the plan, not counted in device_bytes) */
 } wfp_info;
 
 typedef struct wfp_plan_s* wfp_plan;
@@ -255,15 +263,21 @@ wfp_status wfp_checkpoint_save(wfp_plan plan, void* buf, int64_t bytes);
 wfp_status wfp_checkpoint_load(wfp_plan plan, const void* buf, int64_t bytes);
 
 /*
- * Local part of one step without any allocation (the paper has no counterpart: this entry point
- * exists for callers that cannot allocate memory when they need the result -- code running
- * while a CUDA stream is captured into a graph, where cudaMalloc cannot be captured; code whose
- * device memory all comes from a fixed arena it may not grow; real-time loops where an
- * allocation and the synchronisation it can cause are not allowed).  It evaluates
- *     u_l(x_i, t_n) = sum_{j: 0 < r_ij < delta} sum_l eta_l(r_ij) sigma_j(t_{n-nmax+1+l})   (Sec. 6)
- * from scratch for the given points, with the same quadrature as a plan's local part.
+ * Local part of one step without any allocation.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need the result -- code whose
+ * device memory all comes from a fixed arena or pool that the application reserved up front and
+ * that it may not grow, and real-time loops where an allocation's latency, and the device-wide
+ * synchronisation that cudaMalloc and cudaFree can cause, are not allowed.  A plan allocates its
+ * tables and state in wfp_plan_create; this call instead evaluates, from scratch for the given
+ * points,
+ *     u_l(x_i, t_n) = sum_{j: 0 < r_ij < delta} sum_l eta_l(r_ij) sigma_j(t_{n-nmax+1+l})
+ * with the same quadrature weights eta_l as a plan's local part (delta = W dt).
  *   M, src_xy      sources, 2*M doubles (x, y), device memory; M <= 65536.
- *   Mt, tgt_xy     targets, 2*Mt doubles, device memory; Mt <= 32768 (may alias src_xy).
+ *   Mt, tgt_xy     targets, 2*Mt doubles, device memory; Mt <= 32768 (may alias src_xy).  A target
+ *                  whose distance to a source is at most 1e-12 times the side of the points'
+ *                  bounding square coincides with it and that pair is left out; a target that
+ *                  coincides with two or more sources returns WFP_EUNSUPPORTED, as
+ *                  wfp_plan_create does.
  *   sigma_win      device, [nmax][M] doubles, level-major, oldest level first: row l holds
  *                  sigma_j(t_{n-nmax+1+l}) (zero for levels <= 0).
  *   nmax           W + 1 + p/2 for (dt, band_limit, tol) as wfp_select_params reports; must match.
@@ -271,11 +285,14 @@ wfp_status wfp_checkpoint_load(wfp_plan plan, const void* buf, int64_t bytes);
  *   u_local        device, Mt doubles (output).
  *   stream         cudaStream_t or NULL.
  * Scratch: one file-scope device array of about 17 MiB, held by every GPU that loads the
- * library until exit, holds the pair list (at most 65536 pairs 0 < r < delta), the weights and
- * the tables; larger problems return WFP_EINVAL with a message.  The first call on a device looks
- * up the array's address (cudaGetSymbolAddress) and must come before any stream capture.  All
- * calls share the array: calls whose work overlaps on the GPU race.  The call synchronises the
- * stream once (to read the pair count) and returns with the last kernels enqueued on it.
+ * library until exit, holds the pair list (at most 65536 pairs with 0 < r < delta), the weights
+ * and the tables; more sources or targets than the limits above, or more pairs, return
+ * WFP_EINVAL with a message.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current.  All calls share the array and it keeps the
+ * last call's contents: calls whose work overlaps on the GPU (other streams, other threads) race
+ * on it.  The call synchronises the stream once (to read the pair count back) and returns with
+ * the last kernels enqueued on it.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.
  */
 wfp_status wfp_local_noalloc(int64_t M, const double* src_xy, int64_t Mt, const double* tgt_xy,
                              const double* sigma_win, int nmax, double dt, double band_limit, double tol,

@@ -82,6 +82,16 @@ wfp_status wfp_debug_hankel(double kappa, double A, double Delta, double eps, do
  */
 wfp_status wfp_debug_bounded_wait(double limit_s, int arrive, int* timed_out, double* waited_s);
 
+/*
+ * Measured arithmetic peak of the current GPU (no counterpart in the paper: the denominator of the
+ * roofline of the parts bound by arithmetic rather than memory).  A grid of 8 blocks of 256 threads
+ * per SM runs 8 independent fused multiply-add chains per thread, in FP64 (fp64 = 1) or FP32 (0),
+ * timed with CUDA events on the calling thread's default stream; the best of three launches after
+ * one warm-up is reported.  *tflops = 2 flops per FMA over that time, *ms = its duration.
+ * Allocates and frees a small device buffer; synchronises.  Requires a GPU; WFP_ECUDA on failure.
+ */
+wfp_status wfp_debug_alu_peak(int fp64, double* tflops, double* ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -324,6 +324,11 @@ wfp_status wfp_plan_get_info(wfp_plan plan, wfp_info* info) {
     info->local_form = pl.local_factored ? WFP_LOCAL_FACTORED : WFP_LOCAL_STORED;
     info->local_nc = pl.local_factored ? pl.NC : 0;
     info->n_near_pairs = pl.local_factored ? pl.n_near : 0;
+    info->n_spread_tiles = pl.n_tiles;
+    info->bytes_local = pl.bytes_local;
+    info->bytes_grid = pl.bytes_grid;
+    info->bytes_history = pl.bytes_history;
+    info->bytes_fft_work = pl.bytes_fft_work;
     return WFP_OK;
 }
 

@@ -406,6 +406,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
     CK(upload(mem, &pl.d_tgt_perm, torder));
 
     // ---- neighbour search (Sec. 6: N_delta = {j : 0 < r_ij < delta})
+    const int64_t bytes_before_local = mem.bytes;
     const int form = local_form_of(P, pl.opts);
     if (form < 0) {
         err = "local_form WFP_LOCAL_FACTORED needs nmax <= 32, W >= 2 and 8 (W - 1) M < 2^32";
@@ -581,6 +582,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         }
         CK(cudaStreamSynchronize(cudaStreamPerThread));
     }
+    pl.bytes_local = mem.bytes - bytes_before_local;
 
     // ---- near-history modes: half-plane disk |n| dk <= Km (n2 > 0, or n2 = 0 and n1 >= 0)
     const int Nh = P.Nh;
@@ -731,6 +733,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(upload(mem, &pl.d_fforce, ffor));
         CK(mem.alloc(&pl.d_B, (size_t)P.n_lambda * pl.n_far));
         CK(mem.alloc(&pl.d_aF, (size_t)pl.n_far));
+        pl.bytes_history += (int64_t)((size_t)P.n_lambda * pl.n_far + pl.n_far) * sizeof(double2);
         for (size_t f = 0; f < fm.size(); f++)
             if (fm[f] != (int)f) {  // modes are ordered by |k|, so the far modes are a prefix
                 err = "far modes are not the first modes";
@@ -790,6 +793,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(upload(mem, &pl.d_sforce, sfor));
         CK(upload(mem, &pl.d_sw, sw));
         CK(mem.alloc(&pl.d_Y, (size_t)pl.n_soe_self * pl.n_self));
+        pl.bytes_history += (int64_t)((size_t)pl.n_soe_self * pl.n_self * sizeof(double));
     }
 
     // ---- NUFFT tables: footprints, kernel values, deconvolution factors, spreading tiles
@@ -857,6 +861,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
     }
 
     // ---- grids and cuFFT plans (two-stage pruned transforms)
+    const int64_t bytes_before_grid = mem.bytes;
     {
         const int64_t nf = P.nf, nh2 = P.nf / 2 + 1, nc1 = P.Nh + 1;
         T* sp = nullptr;
@@ -905,10 +910,15 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         for (int i = 0; i < 4; i++) {
             cufftHandle h = (i == 0) ? pl.fftA : (i == 1) ? pl.fftB : (i == 2) ? pl.fftBi : pl.fftAi;
             CKF(cufftSetStream(h, pl.stream));
+            size_t ws = 0;
+            CKF(cufftGetSize(h, &ws));
+            pl.bytes_fft_work += (int64_t)ws;
         }
     }
+    pl.bytes_grid = mem.bytes - bytes_before_grid;
 
     // ---- state
+    const int64_t bytes_before_state = mem.bytes;
     {
         T* w = nullptr;
         CK(mem.alloc(&w, (size_t)M * pl.NW));
@@ -937,6 +947,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(mem.alloc(&pl.d_uself, Mt));
         CK(mem.alloc(&pl.d_u_out, Mt));
     }
+    pl.bytes_history += mem.bytes - bytes_before_state;
     CK(mem.alloc(&pl.d_sched, 2));
     CK(cudaStreamCreateWithFlags(&pl.stream2, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&pl.stream3, cudaStreamNonBlocking));

@@ -44,6 +44,10 @@ struct Plan {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_far = nullptr;
     bool poisoned = false;
     int64_t step = 0;  // completed steps
+    // device footprint by role: local part (pair lists, weights or factored records), fine grids and
+    // spectra, carried state (signal windows and history, mode amplitudes, S levels, far and self
+    // recurrences, outputs); cuFFT work areas (not in mem)
+    int64_t bytes_local = 0, bytes_grid = 0, bytes_history = 0, bytes_fft_work = 0;
     int device = 0;
     DevArena mem;
 

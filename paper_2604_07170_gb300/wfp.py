@@ -45,7 +45,9 @@ class wfp_info(ctypes.Structure):
                 ("far_active", ctypes.c_int), ("precision", ctypes.c_int), ("device_bytes", _c_i64),
                 ("lag_store", ctypes.c_int), ("s_levels", _c_i64), ("spread_tile", ctypes.c_int),
                 ("spread_chunk", ctypes.c_int), ("local_variant", ctypes.c_int), ("local_form", ctypes.c_int),
-                ("local_nc", ctypes.c_int), ("n_near_pairs", _c_i64)]
+                ("local_nc", ctypes.c_int), ("n_near_pairs", _c_i64), ("n_spread_tiles", _c_i64),
+                ("bytes_local", _c_i64), ("bytes_grid", _c_i64), ("bytes_history", _c_i64),
+                ("bytes_fft_work", _c_i64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -59,7 +61,7 @@ EXPORTS = ["wfp_debug_eta_table", "wfp_debug_factored_table", "wfp_opts_default"
            "wfp_profile", "wfp_profile_read", "wfp_local_noalloc", "wfp_debug_eta", "wfp_debug_taps", "wfp_debug_phi",
            "wfp_debug_soe", "wfp_debug_hankel", "wfp_debug_bounded_wait", "wfp_checkpoint_size",
            "wfp_checkpoint_save", "wfp_checkpoint_load", "wfp_server_create", "wfp_server_submit", "wfp_server_tick",
-           "wfp_server_run", "wfp_server_query", "wfp_server_result", "wfp_server_destroy"]
+           "wfp_server_run", "wfp_server_query", "wfp_server_result", "wfp_server_destroy", "wfp_debug_alu_peak"]
 
 SIGNAL_GAUSS3, SIGNAL_ERF = 0, 1
 REQ_PENDING, REQ_ACTIVE, REQ_DONE, REQ_FAILED, REQ_BUILDING = range(5)
@@ -124,6 +126,8 @@ def lib():
         getattr(L, name).restype = ctypes.c_int
     L.wfp_debug_bounded_wait.argtypes = [_c_dbl, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _pd]
     L.wfp_debug_bounded_wait.restype = ctypes.c_int
+    L.wfp_debug_alu_peak.argtypes = [ctypes.c_int, _pd, _pd]
+    L.wfp_debug_alu_peak.restype = ctypes.c_int
     L.wfp_server_create.argtypes = [_c_i64, ctypes.c_int, ctypes.POINTER(wfp_opts), ctypes.POINTER(vp)]
     L.wfp_server_submit.argtypes = [vp, ctypes.POINTER(wfp_request), ctypes.POINTER(_c_i64)]
     L.wfp_server_tick.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
@@ -349,6 +353,13 @@ def debug_factored_table(dt, W, p=20, eps=1e-8, band_limit=0.0, ng=20, precision
     _check(lib().wfp_debug_factored_table(dt, W, p, eps, band_limit, ng, precision, ctypes.byref(nc), _dptr(tail),
                                           _dptr(tab)), "wfp_debug_factored_table")
     return nc.value, float(tail[0]), tab
+
+
+def alu_peak(fp64: bool = True) -> tuple[float, float]:
+    """Measured FMA throughput of the current GPU: (TFLOP/s, ms of the timed launch)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().wfp_debug_alu_peak(int(fp64), ctypes.byref(tf), ctypes.byref(ms)), "wfp_debug_alu_peak")
+    return tf.value, ms.value
 
 
 def debug_eta(r, dt, W, p=20, eps=1e-8, band_limit=0.0, ng=20) -> np.ndarray:

@@ -74,3 +74,31 @@ def test_stored_traffic_entries_match_the_current_kernel_code_or_are_reported_st
         # entries (the FP64 line's dominant kernel) must match the committed code
         if kind == "local":
             assert e["source_hash"] == bench.source_hash(kind), key
+
+
+def test_grid_term_counts_the_band_or_its_written_tiles():
+    # spreading writes and interpolation reads the [nb][nf] band (its non-empty tiles when known)
+    info = _info()
+    m = bench.part_model(info, 10000, 10000, False)
+    assert m["interp"]["bytes"] == 608 * 2048 * 4 + 10000 * (2 * 8 * 4 + 4 + 8)
+    info.update(spread_tile=16, n_spread_tiles=1000)
+    m = bench.part_model(info, 10000, 10000, False)
+    assert m["interp"]["bytes"] == 1000 * 256 * 4 + 10000 * (2 * 8 * 4 + 4 + 8)
+    assert m["spread"]["bytes"] == 1000 * 256 * 4 + 10000 * (2 * 8 * 4 + 4 + 4)
+
+
+def test_launch_count_without_the_lagged_regime():
+    # no lag (T < A+): one spread, no far history
+    info = _info(local_form=2)
+    info.update(lag_active=0, lag_store=0)
+    assert bench.launches_per_step(info, 1) == 11
+
+
+def test_accuracy_of_kept_steps():
+    rng = np.random.default_rng(0)
+    ref = rng.standard_normal((2, 50))
+    kept = np.zeros((2, 200))
+    idx = rng.choice(200, 50, replace=False)
+    kept[:, idx] = ref * (1 + 1e-7)
+    a = bench.accuracy({"kept": kept, "kept_steps": [9, 10]}, idx, ref)
+    assert abs(a["rel_l2_vs_oracle"] - 1e-7) < 1e-12 and a["targets"] == 50 and a["steps"] == [9, 10]
