@@ -1,25 +1,28 @@
 // Plan-free evaluation of the local part of the field for one step, without any allocation.
+// The paper has no counterpart: this exists for callers of the library, not for the method.
 //
-// Who needs this: callers that cannot allocate memory at the time they need the result --
-// code running while a CUDA stream is being captured (cudaMalloc is not a capturable
-// operation), code that owns all device memory through a fixed arena or a pool it may not
-// grow, and real-time loops where an allocation (and the implicit synchronisation it can
-// cause) is not allowed.  wfp_plan_create allocates the plan's tables and state, so such a
-// caller cannot use a plan; wfp_local_noalloc gives it the local part (Sec. 6, Eq. local2) of
-// one step instead, for a source/target set that may change from call to call.
+// Who needs this: callers that cannot allocate device memory at the time they need the result
+// -- code whose device memory all comes from a fixed arena or pool that another part of the
+// application reserved up front and that it may not grow, and real-time loops where an
+// allocation's latency and the device-wide synchronisation that cudaMalloc and cudaFree can
+// cause are not allowed.  wfp_plan_create allocates the plan's tables and state, so such a
+// caller cannot use a plan; wfp_local_noalloc gives it the local part of one step instead (the
+// same quadrature weights as a plan's local part), for a source/target set that may change
+// from call to call.
 //
 // Scratch: every intermediate (bounding box, per-target pair counts and offsets, the pair
 // list, the quadrature weights and the quadrature tables) lives in one file-scope
 // `static __device__` array, g_noalloc_scratch, of kScratchBytes bytes.  Every GPU that loads
-// this library holds that array until the process exits.  Its device address is looked up
-// with cudaGetSymbolAddress once per device, by the first call made with that device current;
-// that first call must therefore come before any stream capture.  All calls share the array
-// and it keeps the last call's contents: two calls whose work overlaps on the GPU (different
-// streams, or different host threads) race on it.  Every region is fully written before it is
-// read, so none needs clearing between calls.
+// this library holds that array until the process exits.  In host code the array's name is
+// only a host-side stand-in, so its device address is looked up with cudaGetSymbolAddress once
+// per device, by the first call made with that device current, and passed to the kernels.  All
+// calls share the array and it keeps the last call's contents: two calls whose work overlaps on
+// the GPU (different streams, or different host threads) race on it.  The count of targets that
+// coincide with more than one source is cleared by the first kernel of every call; every other
+// region is fully written before it is read.
 //
 // No cudaMalloc / cudaFree / allocating library routine is called, on the device or on the
-// host: host-side tables are built in fixed-size stack buffers.
+// host: host-side tables are built in fixed-size static buffers.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -47,7 +50,7 @@ constexpr int kMaxDevices = 64;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kTabDoubles = (size_t)kPhiPanels * (kPhiDeg + 1) + (size_t)kNaLevels * (kLsDeg + 1) + 2 * kNaGL + 32;
-constexpr size_t kOffHdr = 0;  // 4 doubles (bounding box) + 1 int64 (pair total)
+constexpr size_t kOffHdr = 0;  // 4 doubles (bounding box), pair total, multiply-coincident target count
 constexpr size_t kOffRow = 256;
 constexpr size_t kOffCnt = kOffRow + align256((kNaMaxTargets + 1) * sizeof(int64_t));
 constexpr size_t kOffCol = kOffCnt + align256(kNaMaxTargets * sizeof(int));
@@ -67,9 +70,11 @@ void* g_dev_ptr[kMaxDevices] = {};    // device address of g_noalloc_scratch, pe
 double g_tab[kTabDoubles];            // host copy of the quadrature tables of the last call
 double g_tab_key[6] = {-1, -1, -1, -1, -1, -1};
 
-// bounding box of sources and targets -> hdr[0..3] = xmin, xmax, ymin, ymax (one block)
+// bounding box of sources and targets -> hdr[0..3] = xmin, xmax, ymin, ymax (one block); clears
+// the count of targets that coincide with more than one source (read back with the pair total)
 __global__ void k_na_bbox(int64_t M, const double* __restrict__ src, int64_t Mt, const double* __restrict__ tgt,
-                          double* __restrict__ hdr) {
+                          double* __restrict__ hdr, unsigned long long* __restrict__ n_multi) {
+    if (threadIdx.x == 0) *n_multi = 0;
     __shared__ double s[4][256];
     double a = 1e300, b = -1e300, c = 1e300, d = -1e300;
     for (int64_t i = threadIdx.x; i < M + Mt; i += blockDim.x) {
@@ -96,22 +101,24 @@ __global__ void k_na_bbox(int64_t M, const double* __restrict__ src, int64_t Mt,
     if (threadIdx.x < 4) hdr[threadIdx.x] = s[threadIdx.x][0];
 }
 
-// pass 0: count pairs 0 < r < delta per target (brute force); pass 1: write them in source order.
-// A pair is coincident (excluded, Eq. exactSol) when r <= 1e-12 of the bounding square's side.
+// pass 0: count pairs 0 < r < delta per target (brute force) and the targets that coincide with
+// more than one source (a plan rejects those too); pass 1: write the pairs in source order.  A pair
+// is coincident (excluded, as a plan excludes it) when r <= 1e-12 of the bounding square's side.
 __global__ void k_na_pairs(int pass, int64_t M, const double* __restrict__ src, int64_t Mt,
                            const double* __restrict__ tgt, double delta, const double* __restrict__ hdr,
                            int* __restrict__ cnt, const int64_t* __restrict__ rowptr, int* __restrict__ col,
-                           double* __restrict__ rr) {
+                           double* __restrict__ rr, unsigned long long* __restrict__ n_multi) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Mt) return;
     double side = fmax(hdr[1] - hdr[0], hdr[3] - hdr[2]);
     double rc = 1e-12 * side;
     double x = tgt[2 * i], y = tgt[2 * i + 1];
     int64_t o = pass ? rowptr[i] : 0;
-    int c = 0;
+    int c = 0, coincident = 0;
     for (int64_t j = 0; j < M; j++) {
         double dx = x - src[2 * j], dy = y - src[2 * j + 1];
         double d2 = dx * dx + dy * dy;
+        if (d2 <= rc * rc) coincident++;
         if (d2 <= rc * rc || !(d2 < delta * delta)) continue;
         if (pass) {
             col[o + c] = (int)j;
@@ -119,10 +126,13 @@ __global__ void k_na_pairs(int pass, int64_t M, const double* __restrict__ src, 
         }
         c++;
     }
-    if (!pass) cnt[i] = c;
+    if (!pass) {
+        cnt[i] = c;
+        if (coincident > 1) atomicAdd(n_multi, 1ull);
+    }
 }
 
-// exclusive scan of the per-target counts (one block) -> rowptr[0..Mt], total in hdr slot 4
+// exclusive scan of the per-target counts (one block) -> rowptr[0..Mt], and the pair total
 __global__ void k_na_scan(int64_t Mt, const int* __restrict__ cnt, int64_t* __restrict__ rowptr,
                           int64_t* __restrict__ total) {
     __shared__ int64_t part[1024];
@@ -231,6 +241,7 @@ extern "C" wfp_status wfp_local_noalloc(int64_t M, const double* src_xy, int64_t
     unsigned char* base = (unsigned char*)g_dev_ptr[dev];
     double* hdr = (double*)(base + kOffHdr);
     int64_t* d_total = (int64_t*)(base + kOffHdr + 4 * sizeof(double));
+    unsigned long long* d_multi = (unsigned long long*)(d_total + 1);  // read back with d_total
     int64_t* rowptr = (int64_t*)(base + kOffRow);
     int* cnt = (int*)(base + kOffCnt);
     int* col = (int*)(base + kOffCol);
@@ -254,18 +265,21 @@ extern "C" wfp_status wfp_local_noalloc(int64_t M, const double* src_xy, int64_t
     const double delta = W * dt;
     cudaError_t e = cudaMemcpyAsync(tab, g_tab, sizeof(g_tab), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return na_fail(WFP_ECUDA, "wfp_local_noalloc: table upload failed");
-    k_na_bbox<<<1, 256, 0, s>>>(M, src_xy, Mt, tgt_xy, hdr);
+    k_na_bbox<<<1, 256, 0, s>>>(M, src_xy, Mt, tgt_xy, hdr, d_multi);
     k_na_pairs<<<(unsigned)((Mt + 127) / 128), 128, 0, s>>>(0, M, src_xy, Mt, tgt_xy, delta, hdr, cnt, nullptr,
-                                                            nullptr, nullptr);
+                                                            nullptr, nullptr, d_multi);
     k_na_scan<<<1, 1024, 0, s>>>(Mt, cnt, rowptr, d_total);
-    int64_t total = -1;
-    e = cudaMemcpyAsync(&total, d_total, sizeof(total), cudaMemcpyDeviceToHost, s);
+    int64_t counts[2] = {-1, -1};  // pair total, targets coinciding with more than one source
+    e = cudaMemcpyAsync(counts, d_total, sizeof(counts), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return na_fail(WFP_ECUDA, "wfp_local_noalloc: pair count failed");
+    const int64_t total = counts[0];
+    if (counts[1] != 0)
+        return na_fail(WFP_EUNSUPPORTED, "wfp_local_noalloc: a target coincides with more than one source");
     if (total > kNaMaxPairs)
         return na_fail(WFP_EINVAL, "wfp_local_noalloc: more than 65536 local pairs (fixed scratch); split the targets");
     k_na_pairs<<<(unsigned)((Mt + 127) / 128), 128, 0, s>>>(1, M, src_xy, Mt, tgt_xy, delta, hdr, cnt, rowptr, col,
-                                                            rr);
+                                                            rr, d_multi);
     if (total > 0) k_na_eta<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(total, rr, dt, W, p, nm, tab, eta);
     k_na_local<<<(unsigned)((Mt * 32 + 255) / 256), 256, 0, s>>>(M, Mt, nm, rowptr, col, eta, sigma_win, u_local);
     e = cudaGetLastError();
