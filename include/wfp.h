@@ -82,9 +82,11 @@ enum { WFP_FP64 = 0, WFP_MIXED = 1 };
  *                 last L + W levels of S per mode in device memory; WFP_LAG_AUTO (0, default) stores
  *                 when that history takes at most 40% of the free device memory, else recomputes.
  *   spread_tile   side of the grid tile one CTA spreads onto (8, 16 or 32); 0 => chosen at plan time
- *                 by timing each.  spread_chunk: sources staged in shared memory per round (32 or 64);
- *                 0 => timed likewise.  Every grid point sums its sources in ascending internal order
- *                 whatever the tiling, so these choices do not change any result bit.
+ *                 by timing each.  spread_chunk: entries of a tile's source list each warp scans per
+ *                 round (32 or 64); 0 => timed likewise.  Every grid point sums the sources that cover
+ *                 it in one fixed order (by the residue of the source index modulo 4, ascending index
+ *                 within a residue class, the four partial sums added in class order) whatever the
+ *                 tiling, so these choices do not change any result bit.
  *   local_variant kernel of the local part when nmax <= 32: 1 = warp-vector loads, 2..5 = weight rows
  *                 staged into shared memory by bulk asynchronous copies (four stage/CTA shapes);
  *                 0 => the fastest, timed at plan time.  All variants give the same bits.
@@ -252,8 +254,9 @@ wfp_status wfp_select_params(double halfside, double dt, int64_t Nt, double band
  *   wfp_checkpoint_size: *bytes receives the buffer size the plan needs.
  *   wfp_checkpoint_save: synchronises the plan's stream and copies the state into buf (bytes >= size).
  *   wfp_checkpoint_load: copies a saved state into a plan created from the same inputs and options
- *                        (checked against a fingerprint of the derived parameters and sizes; a
- *                        mismatch returns WFP_EINVAL and leaves the plan unchanged).  Stepping then
+ *                        (checked against the derived parameters and sizes and a 64-bit hash of the
+ *                        coordinates, dt, N_t, band limit, tolerance and the options that change
+ *                        results; a mismatch returns WFP_EINVAL and leaves the plan unchanged).  Stepping then
  *                        continues from the saved step and gives the same bits as the plan that was
  *                        saved.
  * Errors: WFP_EINVAL (NULL, short buffer, mismatch), WFP_ESTATE (poisoned plan), WFP_ECUDA.

@@ -92,6 +92,25 @@ wfp_status wfp_plan_create(int64_t M, const double* src_xy, int64_t Mt, const do
     pl.P.precision = pl.opts.precision;
     pl.P.exclude_self = pl.opts.exclude_self != 0;
     pl.use_graph = pl.opts.use_graph != 0;
+    {  // fingerprint of the inputs and of the options that change results (checkpoints carry it)
+        uint64_t hsh = 1469598103934665603ull;  // FNV-1a, 64 bit
+        auto mix = [&hsh](const void* p, size_t n) {
+            const unsigned char* c = (const unsigned char*)p;
+            for (size_t i = 0; i < n; i++) hsh = (hsh ^ c[i]) * 1099511628211ull;
+        };
+        mix(src_xy, sizeof(double) * 2 * M);
+        mix(tgt_xy, sizeof(double) * 2 * Mt);
+        const wfp_opts& o = pl.opts;
+        const double dv[6] = {dt, band_limit, tol, o.eps, o.Kf, o.delta};
+        const double dv2[1] = {o.upsampfac};
+        const int iv[10] = {o.precision, o.W, o.p, o.kernel_width, o.soe_nodes, o.exclude_self,
+                            o.lag_mode, o.local_interp, o.local_form, 0};
+        mix(dv, sizeof(dv));
+        mix(dv2, sizeof(dv2));
+        mix(iv, sizeof(iv));
+        mix(&Nt, sizeof(Nt));
+        pl.inputs_hash = hsh;
+    }
     std::string err;
     // validate the scalar arguments before touching the GPU
     {

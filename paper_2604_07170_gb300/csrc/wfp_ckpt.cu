@@ -16,11 +16,12 @@ struct Section {
     size_t bytes;
 };
 
-constexpr uint64_t kMagic = 0x3154504b43504657ull;  // "WFPCKPT1"
+constexpr uint64_t kMagic = 0x3254504b43504657ull;  // "WFPCKPT2"
 
 // Fingerprint of everything the state layout and meaning depend on
 struct Header {
     uint64_t magic;
+    uint64_t inputs;  // hash of the coordinates, time grid, band limit, tolerance and options
     int64_t step;
     int64_t M, Mt, Nt, n_modes, n_far, n_self, n_soe;
     int64_t R_cur, R_lag, n_hist, NW, lag_store, precision;
@@ -52,6 +53,7 @@ Header header(const Plan& pl) {
     Header h;
     std::memset(&h, 0, sizeof(h));
     h.magic = kMagic;
+    h.inputs = pl.inputs_hash;
     h.step = pl.step;
     h.M = pl.M;
     h.Mt = pl.Mt;

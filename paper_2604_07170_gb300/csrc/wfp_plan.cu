@@ -247,6 +247,13 @@ __global__ void k_taps(int64_t nk, const double* __restrict__ kap, double dt, in
 }
 
 // v -> (hi, lo) float pair rows of length W, or double rows
+
+// H[l][fk] *= f[l] (Hankel coefficients times the tail recurrence's input weight; see the far history)
+__global__ void k_scale_terms(int nlam, int64_t nfk, const double* __restrict__ f, double* __restrict__ H) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < (int64_t)nlam * nfk) H[i] *= f[i / nfk];
+}
+
 // head taps of the far recurrence: ffir[q][k] = sum_l H[l][k] coef[l][q]
 __global__ void k_far_head(int nfk, int nlam, int Wh, const double* __restrict__ H, const double* __restrict__ coef,
                            double* __restrict__ ffir) {
@@ -731,6 +738,10 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(cudaGetLastError());
         CK(upload(mem, &pl.d_fdecay, fdec));
         CK(upload(mem, &pl.d_fforce, ffor));
+        // the step keeps the tail state as Eh_l = E_l / f_l (f_l = a_l r_l^(W-1)), Eh_l <- r_l Eh_l +
+        // S_{n-L-W+1}, and reads it with H_l f_l: two FP64 fused multiply-adds per term and component
+        k_scale_terms<<<nblk((int64_t)nfk * P.n_lambda, 256), 256>>>(P.n_lambda, nfk, pl.d_fforce, pl.d_H);
+        CK(cudaGetLastError());
         CK(mem.alloc(&pl.d_B, (size_t)P.n_lambda * pl.n_far));
         CK(mem.alloc(&pl.d_aF, (size_t)pl.n_far));
         pl.bytes_history += (int64_t)((size_t)P.n_lambda * pl.n_far + pl.n_far) * sizeof(double2);
@@ -775,13 +786,13 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         //   u_self(t_n) = sum_{q<W-1} g_q sigma_{n-1-q} + sum_l (w_l dt / 2 pi) Z_l(t_n),
         //   Z_l(t_{n+1}) = r_l Z_l(t_n) + r_l^W sigma_{n+1-W},
         //   g_q = dt phi((q+1) dt) sum_l (w_l / 2 pi) r_l^(q+1):
-        // one shared W-tap window and a one-tap recurrence per term.
+        // one shared W-tap window and a one-tap recurrence per term.  The state is stored as
+        // Zh_l = Z_l / r_l^W (Zh_l <- r_l Zh_l + sigma_{n+1-W}) and its weight as w_l dt r_l^W / 2 pi.
         const int Wh = P.W - 1;
-        std::vector<double> sdec(pl.n_soe_self), sfor(pl.n_soe_self), sw(pl.n_soe_self), head(std::max(Wh, 1), 0.0);
+        std::vector<double> sdec(pl.n_soe_self), sw(pl.n_soe_self), head(std::max(Wh, 1), 0.0);
         for (int l = 0; l < pl.n_soe_self; l++) {
             sdec[l] = std::exp(-lam[l] * P.dt);
-            sfor[l] = std::exp(-lam[l] * P.W * P.dt);
-            sw[l] = q[l] / (2.0 * kPi) * P.dt;
+            sw[l] = q[l] / (2.0 * kPi) * P.dt * std::exp(-lam[l] * P.W * P.dt);
         }
         for (int qq = 0; qq < Wh; qq++) {
             double acc = 0.0;
@@ -790,7 +801,6 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         }
         CK(upload(mem, &pl.d_shead, head));
         CK(upload(mem, &pl.d_sdecay, sdec));
-        CK(upload(mem, &pl.d_sforce, sfor));
         CK(upload(mem, &pl.d_sw, sw));
         CK(mem.alloc(&pl.d_Y, (size_t)pl.n_soe_self * pl.n_self));
         pl.bytes_history += (int64_t)((size_t)pl.n_soe_self * pl.n_self * sizeof(double));

@@ -48,6 +48,7 @@ struct Plan {
     // spectra, carried state (signal windows and history, mode amplitudes, S levels, far and self
     // recurrences, outputs); cuFFT work areas (not in mem)
     int64_t bytes_local = 0, bytes_grid = 0, bytes_history = 0, bytes_fft_work = 0;
+    uint64_t inputs_hash = 0;  // coordinates, dt, N_t, band limit, tol and result-changing options
     int device = 0;
     DevArena mem;
 
@@ -131,11 +132,11 @@ struct Plan {
     int64_t n_far = 0, n_fkappa = 0;
     int* d_far_mode = nullptr;   // [n_far] mode index
     int* d_far_k = nullptr;      // [n_far] far-|k| index
-    double* d_H = nullptr;       // [n_fkappa][n_lambda] Hankel coefficients (Eq. H)
+    double* d_H = nullptr;       // [n_lambda][n_fkappa] Hankel coefficients (Eq. H) times d_fforce[l]
     double* d_ffir = nullptr;    // [n_fkappa][W-1] taps of the newest lagged levels, Phi_q(|k|)
     double* d_fdecay = nullptr;  // [n_lambda] r_l = exp(-lambda_l dt)
     double* d_fforce = nullptr;  // [n_lambda] a_l r_l^(W-1): weight of S_{n-L-W+1} in the tail recurrence
-    double2* d_B = nullptr;      // [n_lambda][n_far] tail state E_l (scaled by exp(A lambda_l), Eq. beta0)
+    double2* d_B = nullptr;      // [n_lambda][n_far] tail state E_l / d_fforce[l] (E_l carries exp(A lambda_l), Eq. beta0)
     double2* d_aF = nullptr;     // [n_far] alpha_F of the current step, added by the mode update
 
     // self term of coincident pairs
@@ -145,9 +146,8 @@ struct Plan {
     int* d_self_src = nullptr;   // internal source
     double* d_shead = nullptr;   // [W-1] shared window weights g_q
     double* d_sdecay = nullptr;  // [n_soe_self] r_l = exp(-mu_l dt)
-    double* d_sforce = nullptr;  // [n_soe_self] r_l^W
-    double* d_sw = nullptr;      // [n_soe_self] SOE weights * dt / (2 pi)
-    double* d_Y = nullptr;       // [n_soe_self][n_self] tail state Z_l
+    double* d_sw = nullptr;      // [n_soe_self] SOE weights * dt * r_l^W / (2 pi)
+    double* d_Y = nullptr;       // [n_soe_self][n_self] tail state Z_l / r_l^W
 
     // outputs (internal target order)
     double* d_uloc = nullptr;

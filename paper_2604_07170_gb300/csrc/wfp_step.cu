@@ -66,6 +66,8 @@ __global__ void __launch_bounds__(256) k_ingest(const int64_t* __restrict__ d_st
 // [d_lo, T] and the trapezoid rule on the grid, arranged as a shared window plus one-tap recurrences:
 //   u_self(t_n) = sum_{q<W-1} g_q sigma_{n-1-q} + sum_l w'_l Z_l(t_n),
 //   Z_l(t_{n+1}) = r_l Z_l(t_n) + r_l^W sigma_{n+1-W}.
+// The state is kept as Zh_l = Z_l / r_l^W, so that a term costs two FP64 fused multiply-adds:
+//   Zh_l(t_{n+1}) = r_l Zh_l(t_n) + sigma_{n+1-W},   u_self += (w'_l r_l^W) Zh_l(t_n).
 constexpr int kMaxWFar = 64;  // W <= 59
 
 constexpr int kSelfGroups = 8;
@@ -77,7 +79,6 @@ __global__ void __launch_bounds__(32 * kSelfGroups) k_self(const int64_t* __rest
                                                            const T* __restrict__ sigwin, int NW, int W, int nsoe,
                                                            const double* __restrict__ shead,
                                                            const double* __restrict__ sdecay,
-                                                           const double* __restrict__ sforce,
                                                            const double* __restrict__ sw, double* __restrict__ Y,
                                                            double* __restrict__ uself) {
     // block (32, G): 32 coincident targets x G interleaved groups of SOE terms
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(32 * kSelfGroups) k_self(const int64_t* __rest
                 const int l = l0 + k * G;
                 if (l < nsoe) {
                     u = fma(sw[l], z[k], u);
-                    Y[(int64_t)l * n_self + s] = fma(sdecay[l], z[k], sforce[l] * x);
+                    Y[(int64_t)l * n_self + s] = fma(sdecay[l], z[k], x);
                 }
             }
         }
@@ -130,67 +131,118 @@ __global__ void k_combine(const int64_t* __restrict__ d_step, int64_t Mt, const 
 __global__ void k_tick(int64_t* d_step) { *d_step += 1; }
 
 // ------------------------------------------------------------------------------- spreading
-// Type-1 spreading onto the fine-grid band, one CTA of TS x TS threads per non-empty TS x TS tile;
-// thread (r, c) owns grid point (r, c) of the tile and sums the sources of the tile's list, which is
-// in ascending internal source order.  A source contributes to a point only through its footprint,
-// so every point sums the same sources in the same order for any TS or CH: no atomics, results
-// independent of the tiling, and the current and lagged transforms of a level bit-identical.
-// Sources are staged CH at a time in shared memory (strength, footprint origin, kernel values).
+// Type-1 spreading onto the fine-grid band, one CTA per non-empty TS x TS tile.  The tile's source
+// list (every source whose w x w footprint meets the tile, ascending internal index) is shared out by
+// the residue of the source index modulo kSpreadWarps: warp c takes the sources j = c (mod
+// kSpreadWarps), in list order, and adds each one's footprint, clipped to the tile, into its own
+// partial tile in shared memory (lanes over footprint columns and rows, kernel values staged in
+// shared memory SM sources at a time).  The tile is then the sum of the partials in warp order.  So
+// every grid point gets
+//     sum_{c < kSpreadWarps} ( sum over the sources j = c (mod kSpreadWarps) that cover it, ascending j )
+// whatever TS or CH: no atomics, results independent of the tiling, and the current and lagged
+// transforms of a level bit-identical.  CH is the number of list entries a warp scans per round.
+constexpr int kSpreadWarps = 4;  // residue classes of the source index (fixed: the sums depend on it)
+constexpr int kSpreadStage = 8;  // sources whose kernel values a warp stages at once
+constexpr int kSpreadKer = 48;   // 2 w values per staged source (w <= 24)
+
 template <typename T, int TS, int CH>
-__global__ void __launch_bounds__(TS * TS) k_spread(const int64_t* __restrict__ d_step, int lag, int L, int64_t M,
-                                                    const T* __restrict__ sighist, int n_hist,
-                                                    const int* __restrict__ tile_xy, const int* __restrict__ tile_ptr,
-                                                    const int* __restrict__ tile_src, const int* __restrict__ src_off,
-                                                    const T* __restrict__ src_ker, int w, T* __restrict__ sp, int nf,
-                                                    int lb0) {
-    int64_t n = *d_step + 1;
-    int64_t lev = lag ? n - L : n;
+__global__ void __launch_bounds__(32 * kSpreadWarps) k_spread(const int64_t* __restrict__ d_step, int lag, int L,
+                                                             int64_t M, const T* __restrict__ sighist, int n_hist,
+                                                             const int* __restrict__ tile_xy,
+                                                             const int* __restrict__ tile_ptr,
+                                                             const int* __restrict__ tile_src,
+                                                             const int* __restrict__ src_off,
+                                                             const T* __restrict__ src_ker, int w, T* __restrict__ sp,
+                                                             int nf, int lb0) {
+    constexpr int P = TS + 1;  // padded row of a partial tile
+    constexpr int SM = kSpreadStage;
+    const int64_t n = *d_step + 1;
+    const int64_t lev = lag ? n - L : n;
     if (lev < 1) return;
     const T* sig = sighist + (lev % n_hist) * M;
-    __shared__ T s_val[CH];
-    __shared__ int s_off[CH];
-    __shared__ T s_ker[CH * 48];
-    const int t = blockIdx.x;
-    const int txy = tile_xy[t];
-    const int tx = txy & 0xffff, ty = txy >> 16;
-    const int colb = tx * TS + (int)(threadIdx.x % TS);
-    const int rowb = ty * TS + (int)(threadIdx.x / TS);
-    T acc = 0;
-    const int a0 = tile_ptr[t], a1 = tile_ptr[t + 1];
+    __shared__ T part[kSpreadWarps][TS * P];
+    __shared__ T stage[kSpreadWarps][SM][kSpreadKer];
+    __shared__ T s_val[kSpreadWarps][SM];
+    __shared__ int s_src[kSpreadWarps][SM], s_off[kSpreadWarps][SM];
+    for (int i = threadIdx.x; i < kSpreadWarps * TS * P; i += blockDim.x) (&part[0][0])[i] = (T)0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;  // lanes below this one
+    const int txy = tile_xy[blockIdx.x];
+    const int tx0 = (txy & 0xffff) * TS, ty0 = (txy >> 16) * TS;
+    const int a0 = tile_ptr[blockIdx.x], a1 = tile_ptr[blockIdx.x + 1];
+    const int w2 = 2 * w;
+    // lanes over a footprint: CL columns (a power of two >= w, at most 32) x 32 / CL rows per pass
+    const int lcl = w <= 8 ? 3 : (w <= 16 ? 4 : 5);
+    const int cx = lane & ((1 << lcl) - 1), ry = lane >> lcl, rpp = 32 >> lcl;
+    T* my = part[warp];
     for (int c0 = a0; c0 < a1; c0 += CH) {
-        const int cn = min(CH, a1 - c0);
-        __syncthreads();
-        for (int i = threadIdx.x; i < cn; i += TS * TS) {
-            int sidx = tile_src[c0 + i];
-            s_val[i] = sig[sidx];
-            s_off[i] = src_off[sidx];
-        }
-        __syncthreads();
-        // x-kernel values are stored pre-multiplied by the source strength
-        for (int i = threadIdx.x; i < cn * 2 * w; i += TS * TS) {
-            int si = i / (2 * w), e = i - si * 2 * w;
-            T v = src_ker[(int64_t)tile_src[c0 + si] * 2 * w + e];
-            s_ker[si * 48 + e] = (e < w) ? s_val[si] * v : v;
-        }
-        __syncthreads();
-        for (int i = 0; i < cn; i++) {
-            const int off = s_off[i];
-            const int dy = rowb - (off >> 16);
-            if ((unsigned)dy < (unsigned)w) {
-                const int dx = colb - (off & 0xffff);
-                const T skx = ((unsigned)dx < (unsigned)w) ? s_ker[i * 48 + dx] : (T)0;
-                acc = fma(skx, s_ker[i * 48 + w + dy], acc);
+#pragma unroll
+        for (int h = 0; h < CH; h += 32) {
+            const int i = c0 + h + lane;
+            const int sidx = (i < a1) ? tile_src[i] : -1;
+            const bool member = sidx >= 0 && (sidx & (kSpreadWarps - 1)) == warp;
+            unsigned mine = __ballot_sync(0xffffffffu, member);
+            while (mine) {  // uniform across the warp
+                // stage the next (up to SM) of this warp's sources, in list order: a member lane whose
+                // rank among the remaining members is below SM writes its source to slot rank
+                const int rank = __popc(mine & lt);
+                const bool take = ((mine >> lane) & 1u) && rank < SM;
+                const int k = min(__popc(mine), SM);
+                if (take) {
+                    s_src[warp][rank] = sidx;
+                    s_off[warp][rank] = src_off[sidx];
+                    s_val[warp][rank] = sig[sidx];
+                }
+                __syncwarp();
+                T kvv[SM], kvw[SM];
+#pragma unroll
+                for (int j = 0; j < SM; j++) {
+                    kvv[j] = (j < k && lane < w2) ? src_ker[(int64_t)s_src[warp][j] * w2 + lane] : (T)0;
+                    kvw[j] = (j < k && lane + 32 < w2) ? src_ker[(int64_t)s_src[warp][j] * w2 + lane + 32] : (T)0;
+                }
+#pragma unroll
+                for (int j = 0; j < SM; j++) {
+                    stage[warp][j][lane] = kvv[j];
+                    if (lane + 32 < kSpreadKer) stage[warp][j][lane + 32] = kvw[j];
+                }
+                __syncwarp();
+                for (int j = 0; j < k; j++) {
+                    const int off = s_off[warp][j];
+                    const int ox = (off & 0xffff) - tx0, oy = (off >> 16) - ty0;  // footprint origin in the tile
+                    const int xx = ox + cx;
+                    if (cx < w && xx >= 0 && xx < TS) {
+                        const T* kv = stage[warp][j];
+                        const T kxs = s_val[warp][j] * kv[cx];  // x-kernel value times the strength
+                        for (int dy = ry; dy < w; dy += rpp) {  // footprint rows dy = ry (mod rpp)
+                            const int yy = oy + dy;
+                            if ((unsigned)yy < (unsigned)TS) {
+                                T* cell = my + yy * P + xx;
+                                *cell = fma(kxs, kv[w + dy], *cell);
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+                mine &= ~__ballot_sync(0xffffffffu, take);
             }
         }
     }
-    sp[(int64_t)rowb * nf + lb0 + colb] = acc;
+    __syncthreads();
+    for (int i = threadIdx.x; i < TS * TS; i += blockDim.x) {
+        const int r = i / TS, c = i - r * TS;
+        T v = part[0][r * P + c];
+#pragma unroll
+        for (int q = 1; q < kSpreadWarps; q++) v += part[q][r * P + c];
+        sp[(int64_t)(ty0 + r) * nf + lb0 + tx0 + c] = v;
+    }
 }
 
 template <typename T, int TS, int CH>
 static void spread_one(const Plan& pl, int lag, int n_tiles, const int* txy, const int* tptr, const int* tsrc, T* sp,
                        cudaStream_t st) {
     const Params& P = pl.P;
-    k_spread<T, TS, CH><<<n_tiles, TS * TS, 0, st>>>(pl.d_step, lag, P.L, pl.M, (const T*)pl.d_sighist, pl.n_hist,
+    k_spread<T, TS, CH><<<n_tiles, 32 * kSpreadWarps, 0, st>>>(pl.d_step, lag, P.L, pl.M, (const T*)pl.d_sighist, pl.n_hist,
                                                        txy, tptr, tsrc, pl.d_src_off, (const T*)pl.d_src_ker, P.w, sp,
                                                        P.nf, P.lb0);
 }
@@ -347,6 +399,12 @@ __global__ void __launch_bounds__(256) k_modes(
 // (Eq. alphakEvolution, FP64) and the type-2 coefficient is written.  (Two threads per mode, one
 // per FIR, gave the same bits with every ring value loaded twice: 6% slower at 10^4 points and 33%
 // at 10^6.)
+// A plan whose run ends before the lag switches on (COMPACT: N_t dt < A+ - delta) never removes a
+// level, so there is nothing to round alike: its FIRs are plain FP32 fused multiply-add sums with the
+// taps' high parts, four levels in flight.  Their rounding (a relative ~1e-7 perturbation of h each
+// step, the size of the FP32 rounding of the S levels themselves) enters alpha once and is carried
+// with it, and the kernel reads its ring at the memory rate instead of being bound by the
+// double-float arithmetic.
 __device__ __forceinline__ void ldg_v8f(const float* p, float4& a, float4& b) {
     asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
@@ -405,54 +463,80 @@ __global__ void __launch_bounds__(256) k_modes_one(
     // h: (hxh, hxl, hyh, hyl); g: (gxh, gxl, gyh, gyl)
     float hxh = 0.f, hxl = 0.f, hyh = 0.f, hyl = 0.f, gxh = 0.f, gxl = 0.f, gyh = 0.f, gyl = 0.f;
     const float* tk = taps + (int64_t)kid * (COMPACT ? 4 : 8) * W;
-    constexpr int U = 2;  // levels whose loads are in flight together
-    int sl = slot, sll = slot_lag;
-    for (int j0 = 0; j0 < W; j0 += U) {
-        float2 a[U], b[U];
-        float4 th[U], tg[U];
+    if constexpr (COMPACT) {
+        constexpr int U4 = 4;  // levels whose loads are in flight together
+        int sc = slot;
+        for (int j0 = 0; j0 < W; j0 += U4) {
+            float2 a[U4];
+            float4 t[U4];
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int j = j0 + u;
-            if (j < W) {
-                if constexpr (COMPACT) {
-                    const float4 t = *(const float4*)(tk + 4 * j);  // {p hi, p lo, q hi, q lo}
-                    th[u] = make_float4(t.x, 0.f, t.y, 0.f);
-                    tg[u] = make_float4(t.z, 0.f, t.w, 0.f);
-                } else {
-                    ldg_v8f(tk + 8 * j, th[u], tg[u]);
-                }
-                if (j == 0) {
-                    a[u] = s_cur;
-                    b[u] = s_lag;
-                } else {
-                    const int s1 = sl - u < 0 ? sl - u + R_cur : sl - u;
-                    a[u] = ring[(int64_t)s1 * n_modes + m];
-                    if (!COMPACT && lag) {
-                        const int s2 = sll - u < 0 ? sll - u + R_lag : sll - u;
-                        b[u] = ring_lag[(int64_t)s2 * n_modes + m];
+            for (int u = 0; u < U4; u++) {
+                const int j = j0 + u;
+                if (j < W) {
+                    t[u] = *(const float4*)(tk + 4 * j);  // {p hi, p lo, q hi, q lo}
+                    if (j == 0) {
+                        a[u] = s_cur;
+                    } else {
+                        const int s1 = sc - u < 0 ? sc - u + R_cur : sc - u;
+                        a[u] = ring[(int64_t)s1 * n_modes + m];
                     }
                 }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-            if (j0 + u < W) {
-                df_acc(hxh, hxl, th[u].x, th[u].z, a[u].x);
-                df_acc(hyh, hyl, th[u].x, th[u].z, a[u].y);
-                if (!COMPACT && lag) {
-                    df_acc(hxh, hxl, -th[u].y, -th[u].w, b[u].x);
-                    df_acc(hyh, hyl, -th[u].y, -th[u].w, b[u].y);
-                }
-                df_acc(gxh, gxl, tg[u].x, tg[u].z, a[u].x);
-                df_acc(gyh, gyl, tg[u].x, tg[u].z, a[u].y);
-                if (!COMPACT && lag) {
-                    df_acc(gxh, gxl, -tg[u].y, -tg[u].w, b[u].x);
-                    df_acc(gyh, gyl, -tg[u].y, -tg[u].w, b[u].y);
+            for (int u = 0; u < U4; u++) {
+                if (j0 + u < W) {
+                    hxh = fmaf(t[u].x, a[u].x, hxh);
+                    hyh = fmaf(t[u].x, a[u].y, hyh);
+                    gxh = fmaf(t[u].z, a[u].x, gxh);
+                    gyh = fmaf(t[u].z, a[u].y, gyh);
                 }
             }
+            sc = sc - U4 < 0 ? sc - U4 + R_cur : sc - U4;
         }
-        sl = sl - U < 0 ? sl - U + R_cur : sl - U;
-        sll = sll - U < 0 ? sll - U + R_lag : sll - U;
+    } else {
+        constexpr int U = 2;  // levels whose loads are in flight together
+        int sl = slot, sll = slot_lag;
+        for (int j0 = 0; j0 < W; j0 += U) {
+            float2 a[U], b[U];
+            float4 th[U], tg[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int j = j0 + u;
+                if (j < W) {
+                    ldg_v8f(tk + 8 * j, th[u], tg[u]);
+                    if (j == 0) {
+                        a[u] = s_cur;
+                        b[u] = s_lag;
+                    } else {
+                        const int s1 = sl - u < 0 ? sl - u + R_cur : sl - u;
+                        a[u] = ring[(int64_t)s1 * n_modes + m];
+                        if (lag) {
+                            const int s2 = sll - u < 0 ? sll - u + R_lag : sll - u;
+                            b[u] = ring_lag[(int64_t)s2 * n_modes + m];
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (j0 + u < W) {
+                    df_acc(hxh, hxl, th[u].x, th[u].z, a[u].x);
+                    df_acc(hyh, hyl, th[u].x, th[u].z, a[u].y);
+                    if (lag) {
+                        df_acc(hxh, hxl, -th[u].y, -th[u].w, b[u].x);
+                        df_acc(hyh, hyl, -th[u].y, -th[u].w, b[u].y);
+                    }
+                    df_acc(gxh, gxl, tg[u].x, tg[u].z, a[u].x);
+                    df_acc(gyh, gyl, tg[u].x, tg[u].z, a[u].y);
+                    if (lag) {
+                        df_acc(gxh, gxl, -tg[u].y, -tg[u].w, b[u].x);
+                        df_acc(gyh, gyl, -tg[u].y, -tg[u].w, b[u].y);
+                    }
+                }
+            }
+            sl = sl - U < 0 ? sl - U + R_cur : sl - U;
+            sll = sll - U < 0 ? sll - U + R_lag : sll - U;
+        }
     }
     const double hx = (double)hxh + (double)hxl, hy = (double)hyh + (double)hyl;
     const double gx = (double)gxh + (double)gxl, gy = (double)gyh + (double)gyl;
@@ -516,6 +600,8 @@ __global__ void __launch_bounds__(256) k_cols_to_band(const C* __restrict__ src,
 // trapezoid interpolant of the lagged S on the grid (exp(A lam) scaling carried in the state):
 //   E_l(t_{n+1}) = r_l E_l(t_n) + f_l S_{n-L-W+1}                  (tail recurrence, one tap)
 //   alpha_F = sum_l H_l(|k|) E_l + sum_{q<W-1} Phi_q(|k|) S_{n-L-q}   (Eq. alphaFApprox + newest levels)
+// with the state kept as Eh_l = E_l / f_l and H_l f_l stored in H: Eh_l <- r_l Eh_l + S_{n-L-W+1},
+// alpha_F = sum_l (H_l f_l) Eh_l + ..., two FP64 fused multiply-adds per term and component.
 // alpha_F goes to aF_out; the mode update adds it to the type-2 coefficient.  With the S history
 // stored every level read here is at least L steps old, so the kernel can run while this step's
 // type-1 transform is computed; with the lag recomputed the newest lagged level n - L is taken from
@@ -524,6 +610,7 @@ __global__ void __launch_bounds__(256) k_cols_to_band(const C* __restrict__ src,
 // shared memory.  Far modes are the first n_far modes (modes are ordered by |k|); H and Phi are
 // stored [term][|k|], so the 32 modes of a warp read neighbours.
 constexpr int kFarGroups = 8;
+constexpr int kFarBatch = 8;  // terms of a thread whose loads are issued together
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kFarGroups) k_far(
@@ -531,8 +618,8 @@ __global__ void __launch_bounds__(32 * kFarGroups) k_far(
     int64_t n_fk, const int* __restrict__ far_k, const int2* __restrict__ mode_n, const double* __restrict__ fac,
     const float* __restrict__ facf, const typename Cplx<T>::type* __restrict__ tc_lag, int from_tc,
     const typename Cplx<T>::type* __restrict__ ring_lag, int R_lag, int lag_off, const double* __restrict__ H,
-    const double* __restrict__ ffir, const double* __restrict__ fdecay, const double* __restrict__ fforce,
-    double2* __restrict__ B, double2* __restrict__ aF_out) {
+    const double* __restrict__ ffir, const double* __restrict__ fdecay, double2* __restrict__ B,
+    double2* __restrict__ aF_out) {
     using C = typename Cplx<T>::type;
     constexpr int G = kFarGroups;
     int64_t n = *d_step + 1;
@@ -579,12 +666,13 @@ __global__ void __launch_bounds__(32 * kFarGroups) k_far(
         }
         const C st = s_S[W - 1][threadIdx.x];
         const double sx = st.x, sy = st.y;
-        // terms l = g, g + G, ... in batches of 8 with every load of a batch issued first
-        for (int l0 = g; l0 < nlam; l0 += 8 * G) {
-            double2 b[8];
-            double hl[8];
+        // terms l = g, g + G, ... in batches with every load of a batch issued first
+        constexpr int NB = kFarBatch;
+        for (int l0 = g; l0 < nlam; l0 += NB * G) {
+            double2 b[NB];
+            double hl[NB];
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
+            for (int u = 0; u < NB; u++) {
                 const int l = l0 + u * G;
                 if (l < nlam) {
                     b[u] = B[(int64_t)l * n_far + f];
@@ -592,12 +680,12 @@ __global__ void __launch_bounds__(32 * kFarGroups) k_far(
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
+            for (int u = 0; u < NB; u++) {
                 const int l = l0 + u * G;
                 if (l < nlam) {
-                    const double d = fdecay[l], fo = fforce[l];
-                    b[u].x = fma(d, b[u].x, fo * sx);
-                    b[u].y = fma(d, b[u].y, fo * sy);
+                    const double d = fdecay[l];
+                    b[u].x = fma(d, b[u].x, sx);
+                    b[u].y = fma(d, b[u].y, sy);
                     B[(int64_t)l * n_far + f] = b[u];
                     aF.x = fma(hl[u], b[u].x, aF.x);
                     aF.y = fma(hl[u], b[u].y, aF.y);
@@ -618,27 +706,32 @@ __global__ void __launch_bounds__(32 * kFarGroups) k_far(
 
 // --------------------------------------------------------------------------- interpolation
 // Type-2 interpolation: u_h(x_i) = sum over the w x w footprint of grid * psi_x psi_y.
-// One warp per target, lane = column offset.
+// G = 32 / H targets per warp, H = 16 lanes per target when w <= 16 (else 32), lane = column offset:
+// a lane sums its column over the footprint's rows, weights it by its column's kernel value, and the
+// H lanes are added by shuffles -- in the grid precision T (FP32 on the mixed path, whose
+// interpolation is FP32; FP64 on the FP64 path), converted to FP64 for the output.
 // u_h(t_{n+1}) goes to slot (n + 1) & 1 of uh, so that step n's output can still read slot n & 1.
-template <typename T>
+template <typename T, int H>
 __global__ void __launch_bounds__(256) k_interp(const int64_t* __restrict__ d_step, int64_t Mt,
                                                 const int* __restrict__ tgt_off, const T* __restrict__ tgt_ker, int w,
                                                 const T* __restrict__ tf, int nf, int lb0, double* __restrict__ uh) {
-    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (i >= Mt) return;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / H;
+    const int lane = threadIdx.x & (H - 1);
+    if (((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / H >= Mt) return;  // whole warp past the end
+    const bool valid = i < Mt;
     uh += ((*d_step + 2) & 1) * Mt;
-    int off = tgt_off[i];
-    int ix0 = off & 0xffff, iy0 = off >> 16;
-    const T* ker = tgt_ker + i * 2 * w;
     T v = 0;
-    if (lane < w) {
+    if (valid && lane < w) {
+        const int off = tgt_off[i];
+        const int ix0 = off & 0xffff, iy0 = off >> 16;
+        const T* ker = tgt_ker + i * 2 * w;
         const T* base = tf + (int64_t)iy0 * nf + lb0 + ix0 + lane;
         for (int dy = 0; dy < w; dy++) v += base[(int64_t)dy * nf] * ker[w + dy];
         v *= ker[lane];
     }
-    double tot = warp_sum((double)v);
-    if (lane == 0) uh[i] = tot;
+#pragma unroll
+    for (int o = H / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (valid && lane == 0) uh[i] = (double)v;
 }
 
 // ================================================================================ drivers
@@ -704,7 +797,7 @@ static wfp_status localpart_t(Plan& pl, cudaStream_t st, std::string& err) {
         ProfScope ps(pl, PP_SELF);
         k_self<T><<<nblk(pl.n_self, 32), dim3(32, kSelfGroups), 0, st>>>(
             pl.d_step, pl.n_self, pl.d_self_tgt, pl.d_self_src, (const T*)pl.d_sigwin, pl.NW, P.W, pl.n_soe_self,
-            pl.d_shead, pl.d_sdecay, pl.d_sforce, pl.d_sw, pl.d_Y, pl.d_uself);
+            pl.d_shead, pl.d_sdecay, pl.d_sw, pl.d_Y, pl.d_uself);
         CK(cudaGetLastError());
     }
     {
@@ -763,7 +856,7 @@ static wfp_status far_t(Plan& pl, cudaStream_t st, std::string& err) {
     k_far<T><<<nblk(pl.n_far, 32), blk, 0, st>>>(
         pl.d_step, pl.n_far, pl.n_modes, P.W, P.L, P.Nh, P.nf, P.n_lambda, pl.n_fkappa, pl.d_far_k, pl.d_mode_n,
         pl.d_fac, pl.d_facf, (const C*)pl.d_tc_lag, pl.lag_store ? 0 : 1, (const C*)pl.d_ring_lag, pl.R_lag,
-        pl.lag_off, pl.d_H, pl.d_ffir, pl.d_fdecay, pl.d_fforce, pl.d_B, pl.d_aF);
+        pl.lag_off, pl.d_H, pl.d_ffir, pl.d_fdecay, pl.d_B, pl.d_aF);
     CK(cudaGetLastError());
     return WFP_OK;
 }
@@ -863,8 +956,14 @@ static wfp_status advance_t(Plan& pl, bool lag_now, std::string& err, cudaEvent_
     }
     ps2.stop();
     ProfScope psi(pl, PP_INTERP);
-    k_interp<T><<<nblk(pl.Mt * 32, 256), 256, 0, st>>>(pl.d_step, pl.Mt, pl.d_tgt_off, (const T*)pl.d_tgt_ker,
-                                                       P.w, (const T*)pl.d_tf, P.nf, P.lb0, pl.d_uh);
+    if (P.w <= 16)
+        k_interp<T, 16><<<nblk(pl.Mt * 16, 256), 256, 0, st>>>(pl.d_step, pl.Mt, pl.d_tgt_off,
+                                                               (const T*)pl.d_tgt_ker, P.w, (const T*)pl.d_tf, P.nf,
+                                                               P.lb0, pl.d_uh);
+    else
+        k_interp<T, 32><<<nblk(pl.Mt * 32, 256), 256, 0, st>>>(pl.d_step, pl.Mt, pl.d_tgt_off,
+                                                               (const T*)pl.d_tgt_ker, P.w, (const T*)pl.d_tf, P.nf,
+                                                               P.lb0, pl.d_uh);
     CK(cudaGetLastError());
     return WFP_OK;
 }

@@ -218,13 +218,17 @@ def test_checkpoint_resume_gives_the_same_bits(precision, lag_mode):
     got = np.stack([b.step(sig[n]) for n in range(150, 220)])
     b.close()
     assert np.array_equal(ref, got)
-    # a plan of other inputs refuses the state and stays usable
-    c = wfp.Plan(wl.src_xy, None, wl.dt, wl.n_steps + 1, wl.band_limit, wl.tol, **kw)
-    with pytest.raises(wfp.WFPError) as ei:
-        c.restore(ck)
-    assert ei.value.code == wfp.WFP_EINVAL
-    c.step(sig[0])
-    c.close()
+    # a plan of other inputs refuses the state and stays usable: another N_t, or the same sizes and
+    # derived parameters with one source moved (caught by the checkpoint's fingerprint of the inputs)
+    moved = wl.src_xy.copy()
+    moved[7] += 1e-3
+    for c in (wfp.Plan(wl.src_xy, None, wl.dt, wl.n_steps + 1, wl.band_limit, wl.tol, **kw),
+              wfp.Plan(moved, None, wl.dt, wl.n_steps, wl.band_limit, wl.tol, **kw)):
+        with pytest.raises(wfp.WFPError) as ei:
+            c.restore(ck)
+        assert ei.value.code == wfp.WFP_EINVAL
+        c.step(sig[0])
+        c.close()
 
 
 def test_one_step_plan_and_zero_signals():
