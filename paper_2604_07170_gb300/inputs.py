@@ -205,3 +205,46 @@ def serve_requests(n: int, seed: int = 0, tol: float = 1e-6, dt: float = 0.1) ->
         out.append(Workload(f"req{i}", xy, par, "gauss3", dt, Nt, band_limit(par, "gauss3", eps), tol,
                             {"box": box, "seed": seed, "index": i}))
     return out
+
+
+# -------------------------------------------------- the paper's grid-target examples
+def paper_grid_workload(kind: str, M: int, n_grid: int, omega_max: float, seed: int = 0, T: float = 8.0,
+                        tol: float = 1e-6, k0dt: float = 1.1) -> tuple[Workload, np.ndarray]:
+    """The large examples of Sec. 7 at a chosen size, in the paper's own units (the domain B = [-1,1]^2,
+    unit wave speed, final time T = 8), with erf-switched sines (Eq. exampleDensities) and an
+    n_grid x n_grid regular target grid covering B:
+      random : sources uniform in B, t0 ~ U[1.5, 7], w = omega_max z^(1/3) (Sec. "Random space-filling
+               sources");
+      circle : M equispaced sources on x(s) = (0.8 cos s + 0.2, 0.8 sin s + 0.2), t0 and w rising linearly
+               in s from 1.5 to 7 and from 0 to omega_max (Sec. "Sources on a circle");
+      wiggly : M sources equispaced in s on x(s) = r(s) (cos s, sin s), r(s) = 0.61 + 0.2 cos 60s
+               - 0.1 sin 20s + 0.05 cos 30s - 0.1 cos 40s, t0 rising in s from 1.5 to 7, w = omega_max
+               z^(1/3) (Sec. "Sources on a complicated closed curve").
+    The paper runs them with omega_max = 300 pi at M = 10^5 (circle) and 10^6; at a smaller M a smaller
+    omega_max keeps the number of sources near a target comparable.  dt is set so that K0 dt = k0dt
+    (1.10 in the paper's runs), with K0 = omega_max + 10 sqrt(ln(1/eps)), eps = tol / 1000."""
+    rng = np.random.Generator(np.random.PCG64(SEED0 + 31337 + 7919 * seed))
+    s = 2.0 * math.pi * np.arange(M) / M
+    par = np.zeros((M, NPAR))
+    if kind == "random":
+        xy = rng.uniform(-1.0, 1.0, size=(M, 2))
+        par[:, 0] = rng.uniform(1.5, 7.0, M)
+        par[:, 1] = omega_max * np.cbrt(rng.uniform(0.0, 1.0, M))
+    elif kind == "circle":
+        xy = np.stack([0.8 * np.cos(s) + 0.2, 0.8 * np.sin(s) + 0.2], axis=1)
+        par[:, 0] = 1.5 + 5.5 * s / (2 * math.pi)
+        par[:, 1] = omega_max * s / (2 * math.pi)
+    elif kind == "wiggly":
+        r = 0.61 + 0.2 * np.cos(60 * s) - 0.1 * np.sin(20 * s) + 0.05 * np.cos(30 * s) - 0.1 * np.cos(40 * s)
+        xy = np.stack([r * np.cos(s), r * np.sin(s)], axis=1)
+        par[:, 0] = 1.5 + 5.5 * s / (2 * math.pi)
+        par[:, 1] = omega_max * np.cbrt(rng.uniform(0.0, 1.0, M))
+    else:
+        raise ValueError(kind)
+    K0 = band_limit(par, "erf", tol / 1000.0)
+    n_steps = int(math.ceil(T * K0 / k0dt))
+    g = np.linspace(-1.0, 1.0, n_grid)
+    tgt = np.stack(np.meshgrid(g, g, indexing="ij"), axis=-1).reshape(-1, 2)
+    wl = Workload(f"paper-{kind}{M}", xy, par, "erf", T / n_steps, n_steps, K0, tol,
+                  {"box": 2.0, "seed": seed, "omega_max": omega_max})
+    return wl, tgt
