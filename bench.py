@@ -191,10 +191,11 @@ def part_model(info: dict, M: int, Mt: int, fp64: bool) -> dict:
     lag = 1 if info["lag_active"] else 0  # the timed window is in the lagged regime when there is one
     spreads = 1 + (lag and not info["lag_store"])  # a second (lagged) spread only without the stored S history
     tapw = 4 * W * s if fp64 else 8 * W * 4     # FIR taps per |k|: FP64, or FP32 hi/lo pairs
-    # the part of the [nb][nf] band that spreading writes and interpolation reads: the non-empty tiles
-    # (the whole band when the tile count is unknown)
+    # the part of the [nb][nf] band that spreading writes and interpolation reads: its non-empty tiles,
+    # all inside the nb x nb sub-box of columns lb0 .. lb0 + nb that the points map to (the whole sub-box
+    # when the tile count is unknown)
     ts = info.get("spread_tile") or 0
-    band = min(nb * nfg, info["n_spread_tiles"] * ts * ts) if info.get("n_spread_tiles") and ts else nb * nfg
+    band = min(nb * nb, info["n_spread_tiles"] * ts * ts) if info.get("n_spread_tiles") and ts else nb * nb
     m = {}
     if info.get("local_form") == 2:
         # factored form: pair records (8 bytes, 16 in FP64), near pairs' stored rows, the per-step
@@ -502,7 +503,13 @@ def serve(args):
     budget = int(0.85 * free_b)
     prec = 0 if args.precision == "fp64" else 1
 
-    def run(arrivals):
+    def check_steps(w):  # outputs kept for the oracle check: mid-run steps and the last one
+        return sorted({max(1, int(0.3 * w.n_steps)), max(1, int(0.6 * w.n_steps)), w.n_steps})
+
+    rng_c = np.random.default_rng(inputs.SEED0 + 6)
+    checked = sorted(rng_c.choice(len(reqs), min(args.serve_check, len(reqs)), replace=False).tolist())
+
+    def run(arrivals, keep=()):
         sv = wfp.Server(budget, args.max_active, precision=prec, **args.plan_opts)
         ids = [None] * len(reqs)
         t0 = time.perf_counter()
@@ -512,7 +519,8 @@ def serve(args):
                 now = time.perf_counter() - t0
                 while nxt < len(reqs) and arrivals[nxt] <= now:
                     w = reqs[nxt]
-                    ids[nxt] = sv.submit(w.src_xy, w.params, w.dt, w.n_steps, w.band_limit, w.tol)
+                    outs = check_steps(w) if nxt in keep else None
+                    ids[nxt] = sv.submit(w.src_xy, w.params, w.dt, w.n_steps, w.band_limit, w.tol, out_steps=outs)
                     nxt += 1
                 a, p = sv.tick()
                 if a == 0 and p == 0:
@@ -520,6 +528,7 @@ def serve(args):
                         break
                     time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
         st = [sv.query(i) for i in ids]
+        kept = {k: sv.result(ids[k]) for k in keep if st[k]["state"] == wfp.REQ_DONE}
         sv.close()
         bad = [i for i, q in enumerate(st) if q["state"] != wfp.REQ_DONE]
         if bad:
@@ -528,15 +537,46 @@ def serve(args):
         wait = np.array([q["t_admit"] - q["t_submit"] for q in st])
         build = np.array([q["t_active"] - q["t_admit"] for q in st])
         span = max(q["t_done"] for q in st) - min(q["t_submit"] for q in st)
-        return lat, wait, span, clk.summary(), build
+        return lat, wait, span, clk.summary(), build, kept
 
-    lat_b, _, span_b, _, build_b = run(np.zeros(len(reqs)))
+    lat_b, _, span_b, _, build_b, _ = run(np.zeros(len(reqs)))
     cap = work.sum() / span_b
     lam = args.serve_load * cap / work.mean()
     rng = np.random.default_rng(inputs.SEED0 + 5)
     arr = np.cumsum(rng.exponential(1.0 / lam, len(reqs)))
     arr -= arr[0]
-    lat, wait, span, clocks, build = run(arr)
+    lat, wait, span, clocks, build, kept = run(arr, checked)
+    # a few random requests against the oracle at three of their steps, on a bounded sample of targets;
+    # error per step relative to max(|u_n|, f max_m |u_m|) as in the parity tests (f = 0.01 FP64, 0.1 mixed)
+    checks = []
+    if not args.no_cpu:
+        import oracle
+        floor_f = 1e-2 if prec == 0 else 1e-1
+        for k in checked:
+            w = reqs[k]
+            steps = check_steps(w)
+            rng_t = np.random.default_rng(inputs.SEED0 + 7 + k)
+            order = rng_t.permutation(w.M)
+            n_t = min(8, w.M)
+            t0 = time.perf_counter()
+
+            def ref_at(idx):
+                ev = np.array([[w.src_xy[i, 0], w.src_xy[i, 1], n * w.dt] for n in steps for i in idx])
+                return oracle.field(w.src_xy, w.params, ev, r_coinc=1e-12 * w.meta["box"]).reshape(len(steps), -1)
+
+            ref = ref_at(order[:n_t])
+            per = (time.perf_counter() - t0) / n_t
+            more = int(min(100, w.M, 30.0 / max(per, 1e-6))) - n_t  # up to 100 targets, ~30 s a request
+            if more > 0:
+                ref = np.concatenate([ref, ref_at(order[n_t:n_t + more])], axis=1)
+                n_t += min(more, w.M - n_t)
+            idx = order[:n_t]
+            got = kept[k][:, idx]
+            norms = np.linalg.norm(ref, axis=1)
+            e = np.linalg.norm(got - ref, axis=1) / np.maximum(norms, floor_f * norms.max())
+            checks.append({"request": int(k), "M": w.M, "N_t": w.n_steps, "box": round(w.meta["box"], 2),
+                           "targets": int(n_t), "steps": steps, "rel_l2_vs_oracle": [float(x) for x in e],
+                           "field_norm_rel_to_peak": [float(x) for x in norms / norms.max()]})
     line = {
         "metric": "serving target-updates/s and request latency (Poisson arrivals)",
         "value": work.sum() / span, "unit": "target-updates/s", "n_gpus": 1, "steps": len(reqs), "warmup": 0,
@@ -553,6 +593,7 @@ def serve(args):
         "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
         "plan_build_s": {"p50": float(np.percentile(build, 50)), "max": float(build.max()), "sum": float(build.sum())},
         "makespan_s": span, "clocks": clocks,
+        "oracle_checks": checks,
     }
     print(json.dumps(line))
 

@@ -77,10 +77,11 @@ def test_stored_traffic_entries_match_the_current_kernel_code_or_are_reported_st
 
 
 def test_grid_term_counts_the_band_or_its_written_tiles():
-    # spreading writes and interpolation reads the [nb][nf] band (its non-empty tiles when known)
+    # spreading writes and interpolation reads the nb x nb sub-box of the [nb][nf] band that the points
+    # map to (its non-empty tiles when known)
     info = _info()
     m = bench.part_model(info, 10000, 10000, False)
-    assert m["interp"]["bytes"] == 608 * 2048 * 4 + 10000 * (2 * 8 * 4 + 4 + 8)
+    assert m["interp"]["bytes"] == 608 * 608 * 4 + 10000 * (2 * 8 * 4 + 4 + 8)
     info.update(spread_tile=16, n_spread_tiles=1000)
     m = bench.part_model(info, 10000, 10000, False)
     assert m["interp"]["bytes"] == 1000 * 256 * 4 + 10000 * (2 * 8 * 4 + 4 + 8)
