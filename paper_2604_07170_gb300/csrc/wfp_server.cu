@@ -80,6 +80,10 @@ struct Request {
     int64_t bytes = 0, plan_bytes = 0;
     double t_submit = 0, t_admit = 0, t_active = 0, t_done = 0;
     std::string err;
+    // admission footprint (stored S history / lagged NUFFT), computed once: counting the local pairs
+    // exactly costs O(M_t x neighbours) host time, too much to repeat on every tick while it waits
+    int64_t est[2] = {0, 0};
+    int est_state = 0;  // 0: not yet computed, 1: valid, -1: invalid request
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // completion of the last enqueued steps
     // plan building on a worker thread (the builder writes plan, buffers, build_status and err,
     // then sets build_done; the server thread reads them only after seeing build_done)
@@ -321,13 +325,17 @@ wfp_status wfp_server_tick(wfp_server sv, int* n_active, int* n_pending) {
                                         (int)(sv->active.size() + sv->building.size()) < sv->max_active &&
                                         (int)sv->building.size() < sv->max_builders;) {
         Request* r = *it;
-        std::string err;
-        int64_t est[2];
-        if (!estimate_bytes(*r, sv->opts, est, err)) {
-            fail_pending(r, err);
+        if (r->est_state == 0) {
+            std::string err;
+            r->est_state = estimate_bytes(*r, sv->opts, r->est, err) ? 1 : -1;
+            if (r->est_state < 0) r->err = err;
+        }
+        if (r->est_state < 0) {
+            fail_pending(r, r->err);
             it = sv->pending.erase(it);
             continue;
         }
+        const int64_t* est = r->est;
         const int64_t free_b = sv->budget - sv->used;
         const bool store = est[1] <= free_b;
         const int64_t need = store ? est[1] : est[0];
