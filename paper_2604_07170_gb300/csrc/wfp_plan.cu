@@ -753,17 +753,11 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(cudaStreamSynchronize(cudaStreamPerThread));
     }
 
-    // ---- self term of coincident pairs: SOE of 1/d on [d_lo, T] with phi(d_lo) <= eps/100
+    // ---- self term of coincident pairs: SOE of 1/d on [dt, T].  The trapezoid rule below evaluates
+    // phi(d) sigma(t - d) / d only at grid delays d = m dt, m >= 1 (phi(0) = 0), so the sum of
+    // exponentials has to represent 1/d there and nowhere closer to 0.
     if (pl.n_self > 0) {
-        double lo = 0.0, hi = P.delta;
-        for (int it = 0; it < 200; it++) {
-            double mid = 0.5 * (lo + hi);
-            if (phi_host(phic.data(), mid, P.delta) > 1e-2 * P.eps)
-                hi = mid;
-            else
-                lo = mid;
-        }
-        double dlo = std::max(lo, 1e-6 * P.delta);
+        const double dlo = P.dt;
         double Tself = std::max(P.T, 2.0 * P.delta);
         // trapezoid in ln(lambda) from lmin = 1e-2 eps / T to lmax = (ln(1/eps) + 3) / d_lo
         std::vector<double> lam, q;
