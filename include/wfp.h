@@ -108,6 +108,13 @@ enum { WFP_FP64 = 0, WFP_MIXED = 1 };
  *                 and wfp_debug_factored_table the table and the tail.  WFP_LOCAL_AUTO (0, default):
  *                 FACTORED on the MIXED path, STORED on the FP64 path (where the stored form needs
  *                 fewer FP64 operations per pair).  FACTORED needs nmax <= 32 and 8 (W - 1) M < 2^32.
+ *   step_order    how a step's two independent branches (local part / self term / output, and the
+ *                 advance: NUFFTs, modes, far history) are issued.  WFP_ORDER_CONCURRENT: on two
+ *                 (three) streams joined at the end of the step, so small problems fill the device;
+ *                 WFP_ORDER_SERIAL: one after the other on the plan's stream, so large problems do not
+ *                 compete for L2 and HBM bandwidth; WFP_ORDER_AUTO (0, default): serial when the local
+ *                 part has at least 2e8 source-target pairs, else concurrent.  The branches share no
+ *                 written buffer, so both orders give the same bits.
  */
 typedef struct {
     int precision;
@@ -128,6 +135,7 @@ typedef struct {
     int local_interp;
     double delta;
     int local_form;
+    int step_order;
 } wfp_opts;
 
 enum { WFP_INTERP_HYBRID = 0, WFP_INTERP_LAGRANGE = 1 };
@@ -135,6 +143,8 @@ enum { WFP_INTERP_HYBRID = 0, WFP_INTERP_LAGRANGE = 1 };
 enum { WFP_LOCAL_AUTO = 0, WFP_LOCAL_STORED = 1, WFP_LOCAL_FACTORED = 2 };
 
 enum { WFP_LAG_AUTO = 0, WFP_LAG_RECOMPUTE = 1, WFP_LAG_STORE = 2 };
+
+enum { WFP_ORDER_AUTO = 0, WFP_ORDER_CONCURRENT = 1, WFP_ORDER_SERIAL = 2 };
 
 /*
  * Derived parameters of a plan (normalised units: the bounding square of all points is
@@ -176,6 +186,7 @@ typedef struct {
     int64_t bytes_history;           /* ... by the carried state: signal windows and history, mode amplitudes
                                         alpha and alpha-dot, the S levels, far and self recurrence states */
     int64_t bytes_fft_work;          /* cuFFT work areas (held by the plan, not counted in device_bytes) */
+    int step_order;                  /* WFP_ORDER_CONCURRENT or WFP_ORDER_SERIAL, as built */
 } wfp_info;
 
 typedef struct wfp_plan_s* wfp_plan;

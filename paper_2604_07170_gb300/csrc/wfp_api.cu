@@ -230,8 +230,17 @@ static wfp_status copy_output(Plan& pl, cudaEvent_t after_output, double* u_dev_
 static wfp_status enqueue_step(Plan& pl, bool do_advance, bool lag_now, cudaEvent_t after_output,
                                double* u_dev_dst, double* u_host_stage, std::string& err) {
     const int which = do_advance ? (lag_now ? 2 : 1) : 3;
-    if (!pl.prof) {  // the whole step as one (graph-captured) fork/join of two streams
+    if (!pl.prof && !pl.serial_step) {  // the whole step as one (graph-captured) fork/join of two streams
         wfp_status st = run_phase(pl, which, [&]() { return step_concurrent(pl, do_advance, lag_now, err); }, err);
+        if (st != WFP_OK) return st;
+        return copy_output(pl, after_output, u_dev_dst, u_host_stage, err);
+    }
+    if (!pl.prof) {  // the whole step (graph-captured) with its branches in sequence on the plan's stream
+        wfp_status st = run_phase(pl, which, [&]() {
+            wfp_status s2 = step_output(pl, err);
+            if (s2 == WFP_OK && do_advance) s2 = step_advance_body(pl, lag_now, err);
+            return s2 == WFP_OK ? step_tick(pl, err) : s2;
+        }, err);
         if (st != WFP_OK) return st;
         return copy_output(pl, after_output, u_dev_dst, u_host_stage, err);
     }
@@ -348,6 +357,7 @@ wfp_status wfp_plan_get_info(wfp_plan plan, wfp_info* info) {
     info->bytes_grid = pl.bytes_grid;
     info->bytes_history = pl.bytes_history;
     info->bytes_fft_work = pl.bytes_fft_work;
+    info->step_order = pl.serial_step ? WFP_ORDER_SERIAL : WFP_ORDER_CONCURRENT;
     return WFP_OK;
 }
 

@@ -95,7 +95,7 @@ static void factored_nc(const Plan& pl, cudaStream_t st) {
             (const T*)pl.d_eta, (const T*)pl.d_siglin, pl.d_uloc);
     } else {
         constexpr int KC = 64 / NC;  // intervals per block of k_ycoef4
-        k_ycoef4<NC><<<dim3(nblk_u(pl.M, 32), (unsigned)((nk + KC - 1) / KC)), 128, 0, st>>>(
+        k_ycoef4<NC><<<nblk_u(pl.M, 32) * (unsigned)((nk + KC - 1) / KC), 128, 0, st>>>(
             pl.M, nk, (const float*)pl.d_siglin, (const float*)pl.d_ctab, (float*)pl.d_ycoef);
         k_local_cheb2<NC><<<nblk_u(pl.Mt * 32, 256), 256, 0, st>>>(
             pl.Mt, pl.d_trow, (const TabPair<float>*)pl.d_tpair, (const float*)pl.d_ycoef, pl.d_rowptr,

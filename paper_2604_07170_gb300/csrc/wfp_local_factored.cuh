@@ -265,14 +265,17 @@ __global__ void __launch_bounds__(256) k_local_cheb2(int64_t Mt, const int64_t* 
 // sources (transposed, [level][source]) times the coefficients of KC = 64 / NC intervals
 // ([level][interval, position]).  Thread (a, b) accumulates sources 4a..4a+3 x positions
 // 4b..4b+3: per level two 16-byte shared loads feed 16 FMAs.  Tiles are filled by coalesced loads.
+// One-dimensional grid, interval groups fastest: the blocks that read one group of source windows
+// run back to back, so the windows come from L2 rather than once per interval group from HBM.
 template <int NC>
 __global__ void __launch_bounds__(128) k_ycoef4(int64_t M, int nk, const float* __restrict__ siglin,
                                                 const float* __restrict__ ctab, float* __restrict__ y) {
     constexpr int KC = 64 / NC, QN = NC / 4;
     __shared__ __align__(16) float sT[32][36];  // [level][source], rows padded
     __shared__ __align__(16) float sc[32][64];  // [level][(interval - k0) * NC + position]
-    const int64_t j0 = (int64_t)blockIdx.x * 32;
-    const int k0 = blockIdx.y * KC, nkc = min(nk - k0, KC);
+    const int nkg = (nk + KC - 1) / KC;
+    const int64_t j0 = (int64_t)(blockIdx.x / nkg) * 32;
+    const int k0 = (int)(blockIdx.x % nkg) * KC, nkc = min(nk - k0, KC);
     for (int t = threadIdx.x; t < 32 * 8; t += 128) {  // 32 windows of 8 vectors
         const int s = t >> 3, v = t & 7;
         const float4 z = (j0 + s < M) ? __ldg((const float4*)(siglin + (j0 + s) * 32) + v) : make_float4(0.f, 0.f, 0.f, 0.f);

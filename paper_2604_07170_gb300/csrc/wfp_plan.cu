@@ -590,6 +590,13 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(cudaStreamSynchronize(cudaStreamPerThread));
     }
     pl.bytes_local = mem.bytes - bytes_before_local;
+    // step order: the two branches of a step compete for L2 and HBM once each fills the device alone
+    if (pl.opts.step_order < WFP_ORDER_AUTO || pl.opts.step_order > WFP_ORDER_SERIAL) {
+        err = "step_order must be WFP_ORDER_AUTO, WFP_ORDER_CONCURRENT or WFP_ORDER_SERIAL";
+        return WFP_EINVAL;
+    }
+    pl.serial_step = pl.opts.step_order == WFP_ORDER_SERIAL ||
+                     (pl.opts.step_order == WFP_ORDER_AUTO && pl.n_pairs >= (int64_t)200000000);
 
     // ---- near-history modes: half-plane disk |n| dk <= Km (n2 > 0, or n2 = 0 and n1 >= 0)
     const int Nh = P.Nh;

@@ -49,6 +49,7 @@ struct Plan {
     // recurrences, outputs); cuFFT work areas (not in mem)
     int64_t bytes_local = 0, bytes_grid = 0, bytes_history = 0, bytes_fft_work = 0;
     uint64_t inputs_hash = 0;  // coordinates, dt, N_t, band limit, tol and result-changing options
+    bool serial_step = false;  // the step's two branches one after the other on the plan's stream
     int device = 0;
     DevArena mem;
 

@@ -18,6 +18,7 @@ FP64, MIXED = 0, 1
 LAG_AUTO, LAG_RECOMPUTE, LAG_STORE = 0, 1, 2
 INTERP_HYBRID, INTERP_LAGRANGE = 0, 1
 LOCAL_AUTO, LOCAL_STORED, LOCAL_FACTORED = 0, 1, 2
+ORDER_AUTO, ORDER_CONCURRENT, ORDER_SERIAL = 0, 1, 2
 
 _c_i64 = ctypes.c_int64
 _c_dbl = ctypes.c_double
@@ -30,7 +31,7 @@ class wfp_opts(ctypes.Structure):
                 ("soe_nodes", ctypes.c_int), ("exclude_self", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("use_graph", ctypes.c_int), ("lag_mode", ctypes.c_int), ("spread_tile", ctypes.c_int),
                 ("spread_chunk", ctypes.c_int), ("local_variant", ctypes.c_int), ("local_interp", ctypes.c_int),
-                ("delta", _c_dbl), ("local_form", ctypes.c_int)]
+                ("delta", _c_dbl), ("local_form", ctypes.c_int), ("step_order", ctypes.c_int)]
 
 
 class wfp_info(ctypes.Structure):
@@ -47,7 +48,7 @@ class wfp_info(ctypes.Structure):
                 ("spread_chunk", ctypes.c_int), ("local_variant", ctypes.c_int), ("local_form", ctypes.c_int),
                 ("local_nc", ctypes.c_int), ("n_near_pairs", _c_i64), ("n_spread_tiles", _c_i64),
                 ("bytes_local", _c_i64), ("bytes_grid", _c_i64), ("bytes_history", _c_i64),
-                ("bytes_fft_work", _c_i64)]
+                ("bytes_fft_work", _c_i64), ("step_order", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

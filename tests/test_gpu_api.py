@@ -47,6 +47,19 @@ def test_graph_replay_equals_direct_launches():
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_serial_and_concurrent_step_orders_give_the_same_bits(precision):
+    # the local branch and the advance share no written buffer, so issuing them one after the other
+    # or on concurrent streams changes no bit (every part active: lag, far history, self term)
+    from paper_2604_07170_gb300 import wfp
+    wl = inputs.small(140, 3.0, 200, seed=23)
+    a, ia = _run(wl, 200, precision=precision, step_order=wfp.ORDER_CONCURRENT)
+    b, ib = _run(wl, 200, precision=precision, step_order=wfp.ORDER_SERIAL)
+    assert ia["step_order"] == wfp.ORDER_CONCURRENT and ib["step_order"] == wfp.ORDER_SERIAL
+    assert ia["lag_active"] and ia["far_active"] and ia["n_self"] > 0
+    assert np.array_equal(a, b)
+
+
 def test_device_and_host_pointers_give_the_same_field():
     import torch
     from paper_2604_07170_gb300 import wfp

@@ -64,6 +64,21 @@ def test_cfg1_all_steps_all_targets():
     assert e.max() <= BAR
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cfg1_geometry_through_the_whole_pulses(precision):
+    # cfg1's 200 points with its signals (pulse centres at t = 8..13) stepped to T = 25: the pulses rise,
+    # pass and leave their tail, and the lag and far history switch on; every 5th step, every target
+    wl = inputs.make("cfg1")
+    wl.n_steps = 250
+    got, info, _ = run_plan(wl, precision=precision)
+    assert info["lag_active"] and info["far_active"] and info["n_self"] == 200
+    steps = list(range(5, 251, 5))
+    ref = oracle_at(wl, None, steps)
+    e = rel_errors(got[np.array(steps) - 1], ref, precision)
+    print(f"\ncfg1 geometry to T = 25, precision {precision}, rel L2:", np.array2string(e, precision=2))
+    assert e.max() <= BAR
+
+
 def test_separate_targets_on_curve():
     # targets distinct from sources (no self term), sources on ellipses
     wl = inputs.small(200, 4.0, 220, seed=2, curve=True)
