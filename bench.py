@@ -12,7 +12,8 @@ updates, type-2 NUFFT).  The timed window ends at a step where the field is well
 
 Metric: target-updates/s = (targets x timed steps) / time.  `value` is device-timed with CUDA
 events on the plan's stream, inputs resident in HBM; `e2e` is measured through the C ABI with
-host buffers (host->device copy of sigma_n and device->host copy of u_n inside the timed region).
+page-locked host buffers (host->device copy of sigma_n and device->host copy of u_n inside the
+timed region).
 Accuracy: relative L2 error against the FP64 CPU oracle (exact retarded field) on random targets
 at two timed steps.  `--impl reference` times that oracle on the host cores on a bounded sample
 of the same workload.
@@ -232,7 +233,7 @@ def measure(wl, precision: str, K: int, Wm: int, e2e_steps: int, prof_steps: int
             plan_opts: dict, timed_end: int = 0) -> dict:
     """Plan the workload, step it to the timed window, time K steps (CUDA events on the plan's
     stream, inputs resident), keep the outputs of the last `keep` timed steps, then per-part event
-    timing and the end-to-end rate through the C ABI with host buffers."""
+    timing and the end-to-end rate through the C ABI with page-locked host buffers."""
     import torch
     from paper_2604_07170_gb300 import wfp
     M, Mt = wl.M, wl.M
@@ -292,9 +293,11 @@ def measure(wl, precision: str, K: int, Wm: int, e2e_steps: int, prof_steps: int
         r["parts"] = plan.profile_read()
         r["prof_steps"] = prof_steps
         plan.profile(False)
-    if e2e_steps > 0:  # end to end through the C ABI with host buffers
-        sig_h = wl.sigma(n + 1, n + 1 + e2e_steps)
-        u_h = np.empty(Mt)
+    if e2e_steps > 0:  # end to end through the C ABI with page-locked host buffers
+        sig_pin = torch.empty((e2e_steps, wl.M), dtype=torch.float64, pin_memory=True)
+        u_pin = torch.empty(Mt, dtype=torch.float64, pin_memory=True)
+        sig_h, u_h = sig_pin.numpy(), u_pin.numpy()
+        sig_h[:] = wl.sigma(n + 1, n + 1 + e2e_steps)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for i in range(e2e_steps):
@@ -419,7 +422,7 @@ def source_hash(kernel: str = "local") -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2604_07170_gb300", "csrc")
     files = {"local": ("wfp_local_kernels.cuh", "wfp_ptx.h", "wfp_dev.h"),
-             "local_factored": ("wfp_local_factored.cuh", "wfp_local_kernels.cuh", "wfp_dev.h")}.get(
+             "local_factored": ("wfp_local_factored.cuh", "wfp_local_kernels.cuh", "wfp_dev.h", "wfp_local.cu")}.get(
         kernel, ("wfp_step.cu", "wfp_dev.h"))
     for fn in files:
         with open(os.path.join(d, fn)) as f:

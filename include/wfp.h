@@ -218,7 +218,9 @@ wfp_status wfp_plan_create(int64_t M, const double* src_xy, int64_t Mt, const do
  *   sigma_n   M doubles (host or device pointer; detected with cudaPointerGetAttributes).
  *   u_n       Mt doubles (host or device pointer).
  * With host pointers the call returns when u_n is written.  With device pointers the work
- * is ordered on the plan's stream and the call returns after enqueueing it.
+ * is ordered on the plan's stream and the call returns after enqueueing it.  Page-locked host
+ * buffers (cudaHostAlloc, cudaMallocHost, cudaHostRegister) are copied to and from the device
+ * directly; pageable ones go through the plan's own page-locked stage (one host memcpy each way).
  * Errors: WFP_EINVAL (NULL pointer), WFP_ESTATE (more than Nt steps, poisoned plan), WFP_ECUDA.
  */
 wfp_status wfp_step(wfp_plan plan, const double* sigma_n, double* u_n);

@@ -64,6 +64,16 @@ wfp_status wfp_debug_phi(double t, double delta, double eps, double* phi, double
 wfp_status wfp_debug_soe(double lam_max, int panels, int ng, double* lam, double* q);
 
 /*
+ * Nodes and weights of the self term's sum of exponentials for 1/d on [dlo, T] (the regularised
+ * self history of coincident pairs, whose kernel at r = 0 is 1/(2 pi d); its recurrence follows the
+ * far history's, Sec. 5): Gauss-Legendre in lambda on [0, 8/T] and composite Gauss-Legendre in
+ * ln(lambda) above, the fewest terms found with relative error <= 0.8 eps on [dlo, T].  Host only.
+ * lam, q: cap doubles each; *n = the number of terms (also set when it exceeds cap, which returns
+ * WFP_EINVAL).
+ */
+wfp_status wfp_debug_self_soe(double dlo, double T, double eps, int cap, double* lam, double* q, int* n);
+
+/*
  * Hankel coefficients of the far history (Sec. 5, Eq. H) at wavenumber magnitude kappa:
  * H_l = q_l exp(-A lam_l) int_0^A J0(kappa r) I0(lam_l r) phi_Delta(A - r) r dr for the dyadic
  * sum of exponentials (lam_max, panels, ng) above, with the composite Gauss-Legendre rule in r

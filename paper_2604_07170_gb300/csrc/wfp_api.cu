@@ -153,6 +153,17 @@ static bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// page-locked host memory (cudaHostAlloc / cudaMallocHost / cudaHostRegister): copied by the GPU's
+// DMA engines directly, with no staging copy on the host
+static bool is_pinned_host(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 static wfp_status poison(Plan& pl, const std::string& msg) {
     pl.poisoned = true;
     return fail(WFP_ECUDA, msg);
@@ -298,9 +309,16 @@ wfp_status wfp_step(wfp_plan plan, const double* sigma_n, double* u_n) {
     if (device_timed_out(pl)) return poison_timeout(pl);
     const int64_t n = pl.step + 1;
     const bool dev_in = is_device_ptr(sigma_n), dev_out = is_device_ptr(u_n);
+    // with a host output the call returns after the whole step, so a pinned input is copied from the
+    // caller's buffer directly; with a device output it returns early and the input goes through the
+    // plan's own stage, which the caller cannot overwrite
+    const bool pin_in = !dev_in && !dev_out && is_pinned_host(sigma_n);
+    const bool pin_out = !dev_out && is_pinned_host(u_n);
     cudaError_t e;
     if (dev_in) {
         e = cudaMemcpyAsync(pl.d_sig_in, sigma_n, pl.M * sizeof(double), cudaMemcpyDeviceToDevice, pl.stream);
+    } else if (pin_in) {
+        e = cudaMemcpyAsync(pl.d_sig_in, sigma_n, pl.M * sizeof(double), cudaMemcpyHostToDevice, pl.stream);
     } else {
         // the pinned staging buffer may still feed the previous step's copy
         cudaStreamSynchronize(pl.stream);
@@ -313,13 +331,13 @@ wfp_status wfp_step(wfp_plan plan, const double* sigma_n, double* u_n) {
     bool adv = n < pl.P.Nt;
     bool lag_now = pl.P.lag_active && (n - pl.P.L >= 1);
     wfp_status st = enqueue_step(pl, adv, lag_now, dev_out ? nullptr : pl.ev_out, dev_out ? u_n : nullptr,
-                                 dev_out ? nullptr : pl.h_u, err);
+                                 dev_out ? nullptr : (pin_out ? u_n : pl.h_u), err);
     if (st != WFP_OK) return poison(pl, err);
     if (!dev_out) {
         e = cudaEventSynchronize(pl.ev_out);
         if (e != cudaSuccess) return poison(pl, std::string("step: ") + cudaGetErrorString(e));
         if (device_timed_out(pl)) return poison_timeout(pl);
-        std::memcpy(u_n, pl.h_u, pl.Mt * sizeof(double));
+        if (!pin_out) std::memcpy(u_n, pl.h_u, pl.Mt * sizeof(double));
     }
     pl.step = n;
     return WFP_OK;
@@ -542,6 +560,18 @@ wfp_status wfp_debug_soe(double lam_max, int panels, int ng, double* lam, double
     if (!lam || !q || panels < 1 || panels > 64 || ng < 1 || ng > 64) return fail(WFP_EINVAL, "bad argument");
     std::vector<double> l, w;
     soe_nodes(lam_max, panels, ng, l, w);
+    std::memcpy(lam, l.data(), l.size() * sizeof(double));
+    std::memcpy(q, w.data(), w.size() * sizeof(double));
+    return WFP_OK;
+}
+
+wfp_status wfp_debug_self_soe(double dlo, double T, double eps, int cap, double* lam, double* q, int* n) {
+    if (!lam || !q || !n || !(dlo > 0.0) || !(T > dlo) || !(eps > 0.0 && eps < 1.0) || cap < 1)
+        return fail(WFP_EINVAL, "bad argument");
+    std::vector<double> l, w;
+    if (!self_soe(dlo, T, eps, l, w)) return fail(WFP_EINVAL, "no candidate sum meets the tolerance");
+    *n = (int)l.size();
+    if ((int)l.size() > cap) return fail(WFP_EINVAL, "more terms than cap");
     std::memcpy(lam, l.data(), l.size() * sizeof(double));
     std::memcpy(q, w.data(), w.size() * sizeof(double));
     return WFP_OK;

@@ -226,21 +226,57 @@ void soe_nodes(double lam_max, int panels, int ng, std::vector<double>& lam, std
     }
 }
 
-// Sum of exponentials for 1/d (r = 0) by the trapezoid rule in s = ln(lambda) applied to
-// 1/d = int exp(s - e^s d) ds over [ln lmin, ln lmax] (step ~h).  The integrand is analytic in
-// the strip |Im s| < pi/2, so the discretisation error decays like exp(-pi^2/h); it decays like
-// e^s below ln lmin (tail ~ lmin d) and doubly exponentially above ln lmax (tail ~ e^{-lmax d}).
-void soe_logtrap(double lmin, double lmax, double h, std::vector<double>& lam, std::vector<double>& q) {
+// Sum of exponentials for 1/d on [dlo, T] (r = 0) from 1/d = int_0^inf exp(-lambda d) dlambda, split
+// at lc (a few times 1/T).  Below lc the integrand is an entire function of lambda with d lc of order
+// one for every d <= T, so n0-point Gauss-Legendre in lambda resolves it: these few terms stand in for
+// the many slowly decaying terms a rule in ln(lambda) would spend there.  Above lc the integrand
+// exp(s - e^s d) in s = ln(lambda) is analytic in the strip |Im s| < pi/2; composite Gauss-Legendre in
+// s (panels of equal width <= ds, n1 nodes each) over [ln lc, ln lmax].  Beyond lmax the dropped tail
+// is exp(-lmax d) / d.  The caller checks the sum against 1/d before using it.
+void soe_inverse(double lc, int n0, double lmax, double ds, int n1, std::vector<double>& lam,
+                 std::vector<double>& q) {
     lam.clear();
     q.clear();
-    double s0 = std::log(lmin), s1 = std::log(lmax);
-    int K = std::max(2, (int)std::ceil((s1 - s0) / h));
-    double hh = (s1 - s0) / K;
-    for (int k = 0; k <= K; k++) {
-        double sk = s0 + k * hh;
-        lam.push_back(std::exp(sk));
-        q.push_back(hh * std::exp(sk));
+    std::vector<double> gx(std::max(n0, n1)), gw(gx.size());
+    gauss_legendre(n0, gx.data(), gw.data());
+    for (int i = 0; i < n0; i++) {
+        lam.push_back(0.5 * lc * (gx[i] + 1.0));
+        q.push_back(0.5 * lc * gw[i]);
     }
+    const double s0 = std::log(lc), s1 = std::max(std::log(lmax), s0 + 1.0);
+    const int P = std::max(1, (int)std::ceil((s1 - s0) / ds));
+    const double hs = (s1 - s0) / P;
+    gauss_legendre(n1, gx.data(), gw.data());
+    for (int pnl = 0; pnl < P; pnl++)
+        for (int i = 0; i < n1; i++) {
+            const double sv = s0 + hs * (pnl + 0.5 * (gx[i] + 1.0));
+            lam.push_back(std::exp(sv));
+            q.push_back(0.5 * hs * gw[i] * std::exp(sv));
+        }
+}
+
+// The self term's sum of exponentials for 1/d on [dlo, T]: soe_inverse with lc = 8 / T and lmax =
+// (ln(1/eps) + 3) / dlo (dropped tail below e^-3 eps), the fewest terms over the node counts and
+// panel widths tried whose relative error on [dlo, T] is within 0.8 eps.  Each term costs the self
+// term two FP64 FMAs per coincident target and step.  False if none meets the tolerance.
+bool self_soe(double dlo, double T, double eps, std::vector<double>& lam, std::vector<double>& q) {
+    lam.clear();
+    q.clear();
+    std::vector<double> tl, tq;
+    const double lmax = (std::log(1.0 / eps) + 3.0) / dlo;
+    bool ok = false;
+    for (int n0 : {8, 10, 12, 14, 16})
+        for (double ds : {2.0, 3.0, 4.0})
+            for (int n1 = 6; n1 <= 24; n1++) {
+                soe_inverse(8.0 / T, n0, lmax, ds, n1, tl, tq);
+                if (ok && tl.size() >= lam.size()) continue;
+                if (soe_max_rel_error(tl, tq, 0.0, dlo, T) <= 0.8 * eps) {
+                    lam.swap(tl);
+                    q.swap(tq);
+                    ok = true;
+                }
+            }
+    return ok;
 }
 
 double soe_max_rel_error(const std::vector<double>& lam, const std::vector<double>& q, double rmax, double tlo,

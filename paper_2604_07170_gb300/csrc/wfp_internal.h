@@ -85,7 +85,12 @@ wfp_status local_params(double dt, double K0, double tol, const wfp_opts& o, dou
 // 1/sqrt(t^2 - r^2) = int_0^inf exp(-lambda t) I0(r lambda) dlambda (Eq. LaplaceIntegral):
 // panels [0, lmax/2^(n-1)], [lmax/2^(n-1), lmax/2^(n-2)], ..., [lmax/2, lmax], ng nodes each.
 void soe_nodes(double lam_max, int panels, int ng, std::vector<double>& lam, std::vector<double>& q);
-void soe_logtrap(double lmin, double lmax, double h, std::vector<double>& lam, std::vector<double>& q);
+// 1/d (r = 0): n0-point Gauss-Legendre in lambda on [0, lc], composite Gauss-Legendre in ln(lambda)
+// (panels of width <= ds, n1 nodes each) on [lc, lmax]
+void soe_inverse(double lc, int n0, double lmax, double ds, int n1, std::vector<double>& lam,
+                 std::vector<double>& q);
+// the self term's sum for 1/d on [dlo, T] to relative eps (false if none of the candidates meets it)
+bool self_soe(double dlo, double T, double eps, std::vector<double>& lam, std::vector<double>& q);
 // max over r in [0, rmax], t in [tlo, thi] of |SOE - 1/sqrt(t^2-r^2)| * sqrt(t^2-r^2)
 double soe_max_rel_error(const std::vector<double>& lam, const std::vector<double>& q, double rmax, double tlo,
                          double thi);

@@ -71,9 +71,14 @@ static void local_attrs_t() {
     bulk_attr<T, D ? 8 : 16, 2, 16>();
 }
 
+// the resident-coefficient contraction takes up to this much dynamic shared memory
+constexpr int kY5MaxSmem = 200 * 1024;
+
 void local_bulk_setup() {
     local_attrs_t<double>();
     local_attrs_t<float>();
+    cudaFuncSetAttribute(k_ycoef5<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kY5MaxSmem);
+    cudaFuncSetAttribute(k_ycoef5<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kY5MaxSmem);
 }
 
 void local_launch(const Plan& pl, int variant, cudaStream_t st) {
@@ -94,9 +99,15 @@ static void factored_nc(const Plan& pl, cudaStream_t st) {
             pl.Mt, pl.d_trow, (const TabPair<T>*)pl.d_tpair, (const T*)pl.d_ycoef, pl.d_rowptr, pl.d_col,
             (const T*)pl.d_eta, (const T*)pl.d_siglin, pl.d_uloc);
     } else {
-        constexpr int KC = 64 / NC;  // intervals per block of k_ycoef4
-        k_ycoef4<NC><<<nblk_u(pl.M, 32) * (unsigned)((nk + KC - 1) / KC), 128, 0, st>>>(
-            pl.M, nk, (const float*)pl.d_siglin, (const float*)pl.d_ctab, (float*)pl.d_ycoef);
+        const size_t smem = (size_t)nk * 32 * NC * sizeof(float);
+        if (smem <= (size_t)kY5MaxSmem) {  // every interval's coefficients fit in shared memory
+            k_ycoef5<NC><<<nblk_u(pl.M, 2 * kY5Threads), kY5Threads, smem, st>>>(
+                pl.M, nk, (const float*)pl.d_siglin, (const float*)pl.d_ctab, (float*)pl.d_ycoef);
+        } else {
+            constexpr int KC = 64 / NC;  // intervals per block of k_ycoef4
+            k_ycoef4<NC><<<nblk_u(pl.M, 32) * (unsigned)((nk + KC - 1) / KC), 128, 0, st>>>(
+                pl.M, nk, (const float*)pl.d_siglin, (const float*)pl.d_ctab, (float*)pl.d_ycoef);
+        }
         k_local_cheb2<NC><<<nblk_u(pl.Mt * 32, 256), 256, 0, st>>>(
             pl.Mt, pl.d_trow, (const TabPair<float>*)pl.d_tpair, (const float*)pl.d_ycoef, pl.d_rowptr,
             pl.d_col, (const float*)pl.d_eta, (const float*)pl.d_siglin, pl.d_uloc);

@@ -316,6 +316,76 @@ __global__ void __launch_bounds__(128) k_ycoef4(int64_t M, int nk, const float* 
     }
 }
 
+// FP32 contraction with the coefficients of every interval resident in shared memory (nk x 32 x
+// NC floats, dynamic) and each thread's two source windows in registers: per interval and group of
+// 16 positions, a level's 16 coefficients are four broadcast 16-byte shared loads feeding 32 FMAs,
+// and each source's 16 results leave as two 32-byte stores (a warp writes 32 consecutive blocks of
+// one interval).  Every output is the FP32 fused multiply-add chain over the levels in ascending
+// order, as in k_ycoef4, so both give the same bits.
+constexpr int kY5Threads = 128;
+__device__ __forceinline__ void stg_v8(float* p, const float* o) {
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(o[0]), "f"(o[1]),
+                 "f"(o[2]), "f"(o[3]), "f"(o[4]), "f"(o[5]), "f"(o[6]), "f"(o[7])
+                 : "memory");
+}
+template <int NC>
+__global__ void __launch_bounds__(kY5Threads, 4) k_ycoef5(int64_t M, int nk, const float* __restrict__ siglin,
+                                                          const float* __restrict__ ctab, float* __restrict__ y) {
+    extern __shared__ __align__(16) float sc5[];  // [interval][level][position]
+    const int nc4 = nk * 32 * NC / 4;
+    for (int t = threadIdx.x; t < nc4; t += kY5Threads) ((float4*)sc5)[t] = __ldg((const float4*)ctab + t);
+    __syncthreads();
+    const int64_t j0 = (int64_t)blockIdx.x * (2 * kY5Threads) + threadIdx.x;
+    const int64_t jj[2] = {j0, j0 + kY5Threads};
+    float w[2][32];
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+        const float4* src = (const float4*)(siglin + jj[s] * 32);
+#pragma unroll
+        for (int v = 0; v < 8; v++) {
+            const float4 z = (jj[s] < M) ? __ldg(src + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+            w[s][4 * v] = z.x;
+            w[s][4 * v + 1] = z.y;
+            w[s][4 * v + 2] = z.z;
+            w[s][4 * v + 3] = z.w;
+        }
+    }
+    for (int k = 0; k < nk; k++) {
+#pragma unroll 1
+        for (int h = 0; h < NC; h += 16) {
+            float acc[2][16];
+#pragma unroll
+            for (int s = 0; s < 2; s++)
+#pragma unroll
+                for (int e = 0; e < 16; e++) acc[s][e] = 0.f;
+            const float* ck = sc5 + (size_t)k * 32 * NC + h;
+#pragma unroll
+            for (int i = 0; i < 32; i++) {
+                float c[16];
+#pragma unroll
+                for (int v = 0; v < 4; v++) {
+                    const float4 q = *(const float4*)(ck + i * NC + 4 * v);
+                    c[4 * v] = q.x;
+                    c[4 * v + 1] = q.y;
+                    c[4 * v + 2] = q.z;
+                    c[4 * v + 3] = q.w;
+                }
+#pragma unroll
+                for (int s = 0; s < 2; s++)
+#pragma unroll
+                    for (int e = 0; e < 16; e++) acc[s][e] = fmaf(w[s][i], c[e], acc[s][e]);
+            }
+#pragma unroll
+            for (int s = 0; s < 2; s++)
+                if (jj[s] < M) {
+                    float* out = y + ((int64_t)k * M + jj[s]) * NC + h;
+                    stg_v8(out, acc[s]);
+                    stg_v8(out + 8, acc[s] + 8);
+                }
+        }
+    }
+}
+
 // position of coefficient c in an FP32 block of NC (16 or 32): the inverse of c = q + 2 (8 v + e)
 // at position 16 v + 8 q + e
 __host__ __device__ inline int cheb2_position(int c) {

@@ -766,17 +766,8 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
     if (pl.n_self > 0) {
         const double dlo = P.dt;
         double Tself = std::max(P.T, 2.0 * P.delta);
-        // trapezoid in ln(lambda) from lmin = 1e-2 eps / T to lmax = (ln(1/eps) + 3) / d_lo
         std::vector<double> lam, q;
-        const double target = P.eps;
-        bool ok = false;
-        for (double h : {0.5, 0.45, 0.42, 0.4, 0.35, 0.3, 0.25}) {
-            soe_logtrap(1e-2 * target / Tself, (std::log(1.0 / target) + 3.0) / dlo, h, lam, q);
-            if (soe_max_rel_error(lam, q, 0.0, dlo, Tself) <= target) {
-                ok = true;
-                break;
-            }
-        }
+        const bool ok = self_soe(dlo, Tself, P.eps, lam, q);
         if (!ok) {
             err = "self-term sum of exponentials did not reach the tolerance";
             return WFP_EINVAL;

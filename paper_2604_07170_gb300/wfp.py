@@ -60,7 +60,7 @@ _lib = None
 EXPORTS = ["wfp_debug_eta_table", "wfp_debug_factored_table", "wfp_opts_default", "wfp_plan_create", "wfp_step", "wfp_destroy", "wfp_plan_get_info",
            "wfp_step_components", "wfp_select_params", "wfp_status_string", "wfp_last_error",
            "wfp_profile", "wfp_profile_read", "wfp_local_noalloc", "wfp_debug_eta", "wfp_debug_taps", "wfp_debug_phi",
-           "wfp_debug_soe", "wfp_debug_hankel", "wfp_debug_bounded_wait", "wfp_checkpoint_size",
+           "wfp_debug_soe", "wfp_debug_self_soe", "wfp_debug_hankel", "wfp_debug_bounded_wait", "wfp_checkpoint_size",
            "wfp_checkpoint_save", "wfp_checkpoint_load", "wfp_server_create", "wfp_server_submit", "wfp_server_tick",
            "wfp_server_run", "wfp_server_query", "wfp_server_result", "wfp_server_destroy", "wfp_debug_alu_peak"]
 
@@ -118,6 +118,7 @@ def lib():
     L.wfp_debug_taps.argtypes = [_c_dbl, _c_dbl, ctypes.c_int, _c_dbl, _c_dbl, _pd, _pd]
     L.wfp_debug_phi.argtypes = [_c_dbl, _c_dbl, _c_dbl, _pd, _pd, _pd]
     L.wfp_debug_soe.argtypes = [_c_dbl, ctypes.c_int, ctypes.c_int, _pd, _pd]
+    L.wfp_debug_self_soe.argtypes = [_c_dbl, _c_dbl, _c_dbl, ctypes.c_int, _pd, _pd, ctypes.POINTER(ctypes.c_int)]
     L.wfp_debug_hankel.argtypes = [_c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_dbl, ctypes.c_int, ctypes.c_int, _pd]
     L.wfp_debug_hankel.restype = ctypes.c_int
     L.wfp_checkpoint_size.argtypes = [vp, ctypes.POINTER(_c_i64)]
@@ -141,7 +142,7 @@ def lib():
         getattr(L, name).restype = ctypes.c_int
     for name in ("wfp_plan_create", "wfp_step", "wfp_destroy", "wfp_plan_get_info", "wfp_step_components",
                  "wfp_profile", "wfp_profile_read",
-                 "wfp_select_params", "wfp_debug_eta", "wfp_debug_taps", "wfp_debug_phi", "wfp_debug_soe"):
+                 "wfp_select_params", "wfp_debug_eta", "wfp_debug_taps", "wfp_debug_phi", "wfp_debug_soe", "wfp_debug_self_soe"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -399,6 +400,13 @@ def debug_bounded_wait(limit_s: float, arrive: bool):
     _check(lib().wfp_debug_bounded_wait(limit_s, 1 if arrive else 0, ctypes.byref(to), ctypes.byref(w)),
            "wfp_debug_bounded_wait")
     return bool(to.value), w.value
+
+
+def debug_self_soe(dlo, T, eps, cap=256):
+    """The self term's sum of exponentials for 1/d on [dlo, T] (host); returns (lam, q)."""
+    lam, q, n = np.zeros(cap), np.zeros(cap), ctypes.c_int()
+    _check(lib().wfp_debug_self_soe(dlo, T, eps, cap, _dptr(lam), _dptr(q), ctypes.byref(n)), "wfp_debug_self_soe")
+    return lam[:n.value].copy(), q[:n.value].copy()
 
 
 def debug_soe(lam_max, panels, ng):

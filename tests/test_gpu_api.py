@@ -81,6 +81,28 @@ def test_device_and_host_pointers_give_the_same_field():
     assert np.array_equal(a, np.stack(got))
 
 
+def test_page_locked_host_buffers_give_the_same_field():
+    # page-locked host buffers are copied by the DMA engines directly (no staging copy); pinned
+    # input with pageable output, and the reverse, take the staged path for one side
+    import torch
+    from paper_2604_07170_gb300 import wfp
+    wl = inputs.small(80, 3.0, 60, seed=14)
+    a, _ = _run(wl, 60)
+    sig = torch.from_numpy(wl.sigma(1, 61)).pin_memory().numpy()
+    out_pin = torch.empty(wl.M, dtype=torch.float64, pin_memory=True).numpy()
+    plan = wfp.Plan(wl.src_xy, None, wl.dt, wl.n_steps, wl.band_limit, wl.tol)
+    got = []
+    for n in range(60):
+        if n % 3 == 0:
+            got.append(plan.step(sig[n], out_pin).copy())
+        elif n % 3 == 1:
+            got.append(plan.step(sig[n]).copy())              # pinned in, pageable out
+        else:
+            got.append(plan.step(np.array(sig[n]), out_pin).copy())  # pageable in, pinned out
+    plan.close()
+    assert np.array_equal(a, np.stack(got))
+
+
 def test_stepping_past_Nt_is_an_error_and_the_plan_survives():
     from paper_2604_07170_gb300 import wfp
     wl = inputs.small(30, 2.0, 5, seed=15)

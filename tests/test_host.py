@@ -95,6 +95,21 @@ def test_dyadic_sum_of_exponentials_accuracy():
     assert worst < 1e-12
 
 
+@pytest.mark.parametrize("dlo,T,eps", [(0.1, 300.0, 1e-9), (0.1, 10.0, 1e-9), (1e-3, 8.0, 1e-12),
+                                       (0.1, 10000.0, 1e-6)])
+def test_self_term_sum_of_exponentials(dlo, T, eps):
+    # the self term's sum for 1/d must hold at every grid delay d = m dt in [dlo, T]; checked here at
+    # those delays and on a dense geometric sample, in extended precision, with its term count:
+    # well under the ~93 terms a trapezoid rule in ln(lambda) from 1e-2 eps / T needs at 1e-9
+    lam, q = wfp.debug_self_soe(dlo, T, eps)
+    assert np.all(lam > 0) and np.all(q > 0)
+    d = np.concatenate([dlo * np.arange(1, int(T / dlo) + 1), np.geomspace(dlo, T, 20000)])
+    s = (q[None, :].astype(np.longdouble) * np.exp(-np.outer(d, lam).astype(np.longdouble))).sum(1)
+    assert np.max(np.abs(s * d - 1)) <= eps
+    if (dlo, T, eps) == (0.1, 300.0, 1e-9):
+        assert lam.size <= 50
+
+
 def test_hankel_and_soe_reproduce_the_truncated_kernel_transform():
     # sum_l H_l e^{A lam_l} e^{-lam_l t} = int_0^A r J0(kappa r) phi_Delta(A - r) / sqrt(t^2 - r^2) dr
     # (Eqs. spectralTK, H, LaplaceApprox), checked against scipy quadrature with the oracle's phi
