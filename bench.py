@@ -190,7 +190,9 @@ def part_model(info: dict, M: int, Mt: int, fp64: bool) -> dict:
     nself, nsoe = info["n_self"], info["n_self_soe"]
     lag = 1 if info["lag_active"] else 0  # the timed window is in the lagged regime when there is one
     spreads = 1 + (lag and not info["lag_store"])  # a second (lagged) spread only without the stored S history
-    tapw = 4 * W * s if fp64 else 8 * W * 4     # FIR taps per |k|: FP64, or FP32 hi/lo pairs
+    # FIR taps per |k|: FP64 {p, q, pA, qA}; mixed, FP32 hi/lo pairs of all four, or FP32 {p, q} when
+    # the lag never switches on
+    tapw = 4 * W * s if fp64 else (8 * W * 4 if lag else 2 * W * 4)
     # the part of the [nb][nf] band that spreading writes and interpolation reads: its non-empty tiles,
     # all inside the nb x nb sub-box of columns lb0 .. lb0 + nb that the points map to (the whole sub-box
     # when the tile count is unknown)
