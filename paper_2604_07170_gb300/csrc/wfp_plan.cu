@@ -238,7 +238,7 @@ __global__ void k_taps(int64_t nk, const double* __restrict__ kap, double dt, in
     if (i >= nk) return;
     if constexpr (sizeof(TT) == 4) {
         if (compact) {  // lag never active: p and q only
-            mode_taps(kap[i], dt, W, lagshift, ngt, sq, wq, f1, f2, TapsCompact{taps + i * 2 * W}, rot + 3 * i);
+            mode_taps(kap[i], dt, W, lagshift, ngt, sq, wq, f1, f2, TapsCompact{taps + i * 4 * W}, rot + 3 * i);
             return;
         }
     }
@@ -663,7 +663,7 @@ static wfp_status build_t(Plan& pl, const std::vector<double>& sxy, const std::v
         CK(upload_tmp(d_f2, f2));
         T* taps = nullptr;
         pl.compact_taps = (sizeof(T) == 4) && !P.lag_active;
-        CK(mem.alloc(&taps, (size_t)pl.n_kappa * (pl.compact_taps ? 2 : (sizeof(T) == 8 ? 4 : 8)) * P.W));
+        CK(mem.alloc(&taps, (size_t)pl.n_kappa * (sizeof(T) == 8 || pl.compact_taps ? 4 : 8) * P.W));
         pl.d_taps = taps;
         CK(mem.alloc(&pl.d_rot, (size_t)pl.n_kappa * 3));
         k_taps<T><<<nblk(pl.n_kappa, 128), 128>>>(pl.n_kappa, d_kap.p, P.dt, P.W, P.Aplus - P.delta, ngt, d_sq.p,

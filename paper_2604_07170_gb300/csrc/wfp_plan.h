@@ -119,8 +119,8 @@ struct Plan {
     int64_t n_modes = 0, n_kappa = 0;
     int2* d_mode_n = nullptr;    // (n1, n2)
     int* d_mode_k = nullptr;     // distinct-|k| index
-    bool compact_taps = false;   // mixed path without lag: taps hold p and q in FP32 only (2 floats per level)
-    void* d_taps = nullptr;      // [n_kappa][4W] p, q, pA, qA (Eq. hggrid), step dt folded in ([n_kappa][2W] p, q when compact_taps; FP32 hi/lo pairs, [8W], on the mixed path with the lag)
+    bool compact_taps = false;   // mixed path without lag: taps hold p and q only (4 floats per level)
+    void* d_taps = nullptr;      // [n_kappa][4W] p, q, pA, qA (Eq. hggrid), step dt folded in (mixed: FP32 hi/lo pairs, [8W]; [4W] of p and q when compact_taps)
     double* d_rot = nullptr;     // [n_kappa][3] cos(k dt), sin(k dt)/k, k sin(k dt)
     double2* d_alpha = nullptr;  // [n_modes]
     double2* d_alphad = nullptr; // [n_modes]

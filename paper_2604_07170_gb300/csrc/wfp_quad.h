@@ -190,13 +190,17 @@ struct TapsInterleaved<float> {
     }
 };
 
-// p and q rounded to FP32 only (plans whose lag never activates, whose FIRs are plain FP32 sums):
-// per level {p, q}, one float2
+// FP32 hi/lo pairs of p and q only (plans whose lag never activates): per level {p hi, p lo},
+// {q hi, q lo} -- one float2 per FIR
 struct TapsCompact {
     float* t;
     WFP_HD void operator()(int m, double p, double q, double, double) const {
-        t[2 * m] = (float)p;
-        t[2 * m + 1] = (float)q;
+        const double v[2] = {p, q};
+        for (int i = 0; i < 2; i++) {
+            const float hi = (float)v[i];
+            t[4 * m + 2 * i] = hi;
+            t[4 * m + 2 * i + 1] = (float)(v[i] - (double)hi);
+        }
     }
 };
 

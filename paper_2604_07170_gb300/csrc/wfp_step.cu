@@ -462,17 +462,18 @@ __global__ void __launch_bounds__(256) k_modes_one(
     }
     // h: (hxh, hxl, hyh, hyl); g: (gxh, gxl, gyh, gyl)
     float hxh = 0.f, hxl = 0.f, hyh = 0.f, hyl = 0.f, gxh = 0.f, gxl = 0.f, gyh = 0.f, gyl = 0.f;
-    const float* tk = taps + (int64_t)kid * (COMPACT ? 2 : 8) * W;
+    const float* tk = taps + (int64_t)kid * (COMPACT ? 4 : 8) * W;
     if constexpr (COMPACT) {
         constexpr int U4 = 4;  // levels whose loads are in flight together
         int sc = slot;
         for (int j0 = 0; j0 < W; j0 += U4) {
-            float2 a[U4], t[U4];
+            float2 a[U4];
+            float4 t[U4];
 #pragma unroll
             for (int u = 0; u < U4; u++) {
                 const int j = j0 + u;
                 if (j < W) {
-                    t[u] = *(const float2*)(tk + 2 * j);  // {p, q}
+                    t[u] = *(const float4*)(tk + 4 * j);  // {p hi, p lo, q hi, q lo}
                     if (j == 0) {
                         a[u] = s_cur;
                     } else {
@@ -486,8 +487,8 @@ __global__ void __launch_bounds__(256) k_modes_one(
                 if (j0 + u < W) {
                     hxh = fmaf(t[u].x, a[u].x, hxh);
                     hyh = fmaf(t[u].x, a[u].y, hyh);
-                    gxh = fmaf(t[u].y, a[u].x, gxh);
-                    gyh = fmaf(t[u].y, a[u].y, gyh);
+                    gxh = fmaf(t[u].z, a[u].x, gxh);
+                    gyh = fmaf(t[u].z, a[u].y, gyh);
                 }
             }
             sc = sc - U4 < 0 ? sc - U4 + R_cur : sc - U4;
