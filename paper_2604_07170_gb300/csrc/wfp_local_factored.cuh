@@ -319,18 +319,28 @@ __global__ void __launch_bounds__(128) k_ycoef4(int64_t M, int nk, const float* 
 // FP32 contraction with the coefficients of every interval resident in shared memory (nk x 32 x
 // NC floats, dynamic) and each thread's two source windows in registers: per interval and group of
 // 16 positions, a level's 16 coefficients are four broadcast 16-byte shared loads feeding 32 FMAs,
-// and each source's 16 results leave as two 32-byte stores (a warp writes 32 consecutive blocks of
-// one interval).  Every output is the FP32 fused multiply-add chain over the levels in ascending
-// order, as in k_ycoef4, so both give the same bits.
+// issued as 16 packed two-lane FMAs (fma.rn.f32x2: each lane an IEEE fused multiply-add), and each
+// source's 16 results leave as two 32-byte stores (a warp writes 32 consecutive blocks of one
+// interval).  Every output is the FP32 fused multiply-add chain over the levels in ascending order,
+// as in k_ycoef4, so both give the same bits.
 constexpr int kY5Threads = 128;
-__device__ __forceinline__ void stg_v8(float* p, const float* o) {
-    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(o[0]), "f"(o[1]),
-                 "f"(o[2]), "f"(o[3]), "f"(o[4]), "f"(o[5]), "f"(o[6]), "f"(o[7])
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ void stg_v4b64(float* p, const unsigned long long* o) {
+    asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(o[0]), "l"(o[1]), "l"(o[2]), "l"(o[3])
                  : "memory");
 }
 template <int NC>
 __global__ void __launch_bounds__(kY5Threads, 4) k_ycoef5(int64_t M, int nk, const float* __restrict__ siglin,
-                                                          const float* __restrict__ ctab, float* __restrict__ y) {
+                                                            const float* __restrict__ ctab, float* __restrict__ y) {
     extern __shared__ __align__(16) float sc5[];  // [interval][level][position]
     const int nc4 = nk * 32 * NC / 4;
     for (int t = threadIdx.x; t < nc4; t += kY5Threads) ((float4*)sc5)[t] = __ldg((const float4*)ctab + t);
@@ -353,34 +363,34 @@ __global__ void __launch_bounds__(kY5Threads, 4) k_ycoef5(int64_t M, int nk, con
     for (int k = 0; k < nk; k++) {
 #pragma unroll 1
         for (int h = 0; h < NC; h += 16) {
-            float acc[2][16];
+            unsigned long long acc[2][8];
 #pragma unroll
             for (int s = 0; s < 2; s++)
 #pragma unroll
-                for (int e = 0; e < 16; e++) acc[s][e] = 0.f;
+                for (int e = 0; e < 8; e++) acc[s][e] = 0ull;
             const float* ck = sc5 + (size_t)k * 32 * NC + h;
 #pragma unroll
             for (int i = 0; i < 32; i++) {
-                float c[16];
+                unsigned long long c[8];
 #pragma unroll
                 for (int v = 0; v < 4; v++) {
-                    const float4 q = *(const float4*)(ck + i * NC + 4 * v);
-                    c[4 * v] = q.x;
-                    c[4 * v + 1] = q.y;
-                    c[4 * v + 2] = q.z;
-                    c[4 * v + 3] = q.w;
+                    const ulonglong2 q = *(const ulonglong2*)(ck + i * NC + 4 * v);
+                    c[2 * v] = q.x;
+                    c[2 * v + 1] = q.y;
                 }
 #pragma unroll
-                for (int s = 0; s < 2; s++)
+                for (int s = 0; s < 2; s++) {
+                    const unsigned long long ww = pk2(w[s][i], w[s][i]);
 #pragma unroll
-                    for (int e = 0; e < 16; e++) acc[s][e] = fmaf(w[s][i], c[e], acc[s][e]);
+                    for (int e = 0; e < 8; e++) acc[s][e] = ffma2(ww, c[e], acc[s][e]);
+                }
             }
 #pragma unroll
             for (int s = 0; s < 2; s++)
                 if (jj[s] < M) {
                     float* out = y + ((int64_t)k * M + jj[s]) * NC + h;
-                    stg_v8(out, acc[s]);
-                    stg_v8(out + 8, acc[s] + 8);
+                    stg_v4b64(out, acc[s]);
+                    stg_v4b64(out + 8, acc[s] + 4);
                 }
         }
     }

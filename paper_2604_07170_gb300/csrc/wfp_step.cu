@@ -538,8 +538,18 @@ __global__ void __launch_bounds__(256) k_modes_one(
             sll = sll - U < 0 ? sll - U + R_lag : sll - U;
         }
     }
-    const double hx = (double)hxh + (double)hxl, hy = (double)hyh + (double)hyl;
-    const double gx = (double)gxh + (double)gxl, gy = (double)gyh + (double)gyl;
+    double hx, hy, gx, gy;
+    if constexpr (COMPACT) {  // plain FP32 sums: no low parts to add
+        hx = (double)hxh;
+        hy = (double)hyh;
+        gx = (double)gxh;
+        gy = (double)gyh;
+    } else {
+        hx = (double)hxh + (double)hxl;
+        hy = (double)hyh + (double)hyl;
+        gx = (double)gxh + (double)gxl;
+        gy = (double)gyh + (double)gyl;
+    }
     const double c = rot[3 * kid], sk = rot[3 * kid + 1], ks = rot[3 * kid + 2];
     const double2 a = alpha[m], ad = alphad[m];
     double2 an, adn;
