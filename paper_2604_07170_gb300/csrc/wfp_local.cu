@@ -99,8 +99,19 @@ static void factored_nc(const Plan& pl, cudaStream_t st) {
             pl.Mt, pl.d_trow, (const TabPair<T>*)pl.d_tpair, (const T*)pl.d_ycoef, pl.d_rowptr, pl.d_col,
             (const T*)pl.d_eta, (const T*)pl.d_siglin, pl.d_uloc);
     } else {
+        // k_ycoef5 gives every block 256 sources: below one block per SM (10^4 points: 40 blocks) the
+        // interval-split k_ycoef4 fills the device better; both give the same bits
+        static std::atomic<int> sm_count{0};
+        int sms = sm_count.load(std::memory_order_relaxed);
+        if (sms == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            sm_count.store(sms, std::memory_order_relaxed);
+        }
         const size_t smem = (size_t)nk * 32 * NC * sizeof(float);
-        if (smem <= (size_t)kY5MaxSmem) {  // every interval's coefficients fit in shared memory
+        if (smem <= (size_t)kY5MaxSmem && (int64_t)nblk_u(pl.M, 2 * kY5Threads) >= sms) {
+            // every interval's coefficients fit in shared memory, and the grid fills the device
             k_ycoef5<NC><<<nblk_u(pl.M, 2 * kY5Threads), kY5Threads, smem, st>>>(
                 pl.M, nk, (const float*)pl.d_siglin, (const float*)pl.d_ctab, (float*)pl.d_ycoef);
         } else {
