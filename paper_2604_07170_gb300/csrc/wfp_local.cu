@@ -71,8 +71,9 @@ static void local_attrs_t() {
     bulk_attr<T, D ? 8 : 16, 2, 16>();
 }
 
-// the resident-coefficient contraction takes up to this much dynamic shared memory
-constexpr int kY5MaxSmem = 200 * 1024;
+// the resident-coefficient contraction takes up to this much dynamic shared memory (two CTAs per SM
+// or more; above it, the interval-split contraction, which gives the same bits)
+constexpr int kY5MaxSmem = 100 * 1024;
 
 void local_bulk_setup() {
     local_attrs_t<double>();
