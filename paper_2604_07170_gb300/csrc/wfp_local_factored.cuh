@@ -30,7 +30,7 @@ struct __align__(16) TabPair<double> {
 // On a delay interval [k dt, (k+1) dt], k >= 1, each weight is a Chebyshev series in the interval's
 // variable x(r): eta_l(r) = sum_c C[k][l][c] T_c(x(r)).  Summing over the levels first,
 //   sum_l eta_l(r_ij) sigma_j,l = sum_c T_c(x_ij) y[k][j][c],   y[k][j][c] = sum_l C[k][l][c] sigma_j,l,
-// so one contraction per source and interval per step (k_ycoef4; k_ycoef in FP64) replaces a weight
+// so one contraction per source and interval per step (k_ycoef5 or k_ycoef4; k_ycoef in FP64) replaces a weight
 // row per pair, and a pair needs only its block index and x: 8 bytes instead of 32 weights.  y holds
 // sources x intervals x NC values; the pairs of neighbouring targets gather the same blocks, mostly
 // from L2.
