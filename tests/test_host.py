@@ -271,6 +271,32 @@ def test_local_weight_table_matches_the_quadrature():
         assert worst <= 1e-13, (dt, W, worst)
 
 
+def test_near_weights_are_smooth_on_dyadic_subintervals():
+    # below dt the weights carry a logarithm of r; on the sub-intervals [dt/2, dt] (variable
+    # sqrt(dt - r), as for the other delay intervals) and [dt/4, dt/2], [dt/8, dt/4] (variable r) they
+    # are analytic, so a 16-term Chebyshev series reproduces them with coefficients no larger than the
+    # weights themselves (what an FP32 factored form of the near pairs needs)
+    from numpy.polynomial import chebyshev as C
+    dt, W, p, eps = 0.1, 23, 16, 1e-9
+    K0 = 2 * np.pi + np.sqrt(2 * np.log(1 / eps))
+    n = 24
+    z = np.cos(np.pi * (np.arange(n) + 0.5) / n)
+    zt = np.linspace(-1.0, 1.0, 7)
+    for a, b, bound in ((0.5, 1.0, 1e-7), (0.25, 0.5, 1e-12), (0.125, 0.25, 1e-12)):
+        def r_of(zz):
+            if a == 0.5:
+                v = 0.5 * (zz + 1) * np.sqrt((b - a) * dt)
+                return b * dt - v * v
+            return (a + (b - a) * 0.5 * (zz + 1)) * dt
+        E = np.array([wfp.debug_eta(r, dt, W, p, eps, K0) for r in r_of(z)])
+        coef = np.array([C.chebfit(z, E[:, l], 15) for l in range(E.shape[1])])
+        Et = np.array([wfp.debug_eta(r, dt, W, p, eps, K0) for r in r_of(zt)])
+        fit = np.array([C.chebval(zt, coef[l]) for l in range(E.shape[1])]).T
+        scale = np.abs(E).max()
+        assert np.abs(fit - Et).max() <= bound * scale, (a, b)
+        assert np.abs(coef).sum(axis=1).max() <= 1.05 * scale, (a, b)
+
+
 def test_factored_local_series_cut_against_the_quadrature():
     # the factored local part (mixed path) keeps the first NC Chebyshev coefficients of each delay
     # interval's weight series; the dropped tail must bound the error against the direct quadrature
